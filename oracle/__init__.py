@@ -1,0 +1,248 @@
+"""FP64 CPU oracle for the linear tetrahedron orbital-resolved DOS.
+
+TEST INFRASTRUCTURE ONLY: this package is the slow, plain reference that the
+CUDA path is checked against. Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+It shares no code with ``paper_1710_10789_gb300`` and neither imports the other.
+
+Pieces and the passages they follow (arXiv:1710.10789):
+  * ``hamiltonian`` / ``eig``: H(k) from the hopping form of Eq. (1) and its
+    dense diagonalisation (Sec. II.A); orbital weights b = |a|^2, Eq. (3).
+  * ``corner_weights``: the five energy cases of Sec. II.C (C code).
+  * ``dos``: Eqs. (8)-(9), point values dw/dE or bin averages of w (C code).
+  * ``weight_moments`` / ``dos_bin_grad``: derivative of the bin-averaged DOS
+    with respect to corner energies and orbital weights, from the integral
+    definition of the corner weights (C code).
+  * ``eig_backward``: first-order perturbation theory of the Hermitian
+    eigenproblem, chained to the hopping parameters of Eq. (1).
+
+Every numerical convention (grid, corner labels, region boundaries, the
+corrected dw3/dE term) is listed in the header of ``tetra_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBPATH = os.path.join(_LIBDIR, "liboracle.so")
+_SRC = os.path.join(_HERE, "tetra_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+#: Regularisation of 1/(e_n - e_m) in the eigenvector derivative:
+#: F = d / (d^2 + ETA^2) with d in eV (reading of degenerate pairs).
+ETA = 1e-8
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into oracle/_lib/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIBPATH) or os.path.getmtime(_LIBPATH) < os.path.getmtime(_SRC):
+        tmp = _LIBPATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIBPATH)
+            d = ctypes.POINTER(ctypes.c_double)
+            i = ctypes.c_int
+            lib.oracle_corner_weights.argtypes = [d, ctypes.c_double, ctypes.c_double, d, d]
+            lib.oracle_corner_weights.restype = None
+            lib.oracle_weight_moments.argtypes = [d, ctypes.c_double, ctypes.c_double, d]
+            lib.oracle_weight_moments.restype = None
+            lib.oracle_dos_range.argtypes = [i, i, i, i, i, d, d, i, i, d, d, i, i, d, i]
+            lib.oracle_dos_range.restype = i
+            lib.oracle_dos_bin_grad.argtypes = [i, i, i, i, i, d, d, i, d, d, d, d, d]
+            lib.oracle_dos_bin_grad.restype = i
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# ---------------------------------------------------------------- per tetrahedron
+def corner_weights(e_sorted, E: float, f: float):
+    """(w[4], dw/dE[4]) of one tetrahedron with sorted corner energies."""
+    lib = _load()
+    e = _c64(e_sorted)
+    w = np.zeros(4)
+    dw = np.zeros(4)
+    lib.oracle_corner_weights(_p(e), float(E), float(f), _p(w), _p(dw))
+    return w, dw
+
+
+def weight_moments(e_sorted, E: float, f: float) -> np.ndarray:
+    """M[l, i] with d w_l / d e_i = -M[l, i] (sorted indices)."""
+    lib = _load()
+    e = _c64(e_sorted)
+    M = np.zeros((4, 4))
+    lib.oracle_weight_moments(_p(e), float(E), float(f), _p(M))
+    return M
+
+
+# ---------------------------------------------------------------- model + eig
+def hamiltonian(model: dict, n1: int, n2: int, n3: int) -> np.ndarray:
+    """H(k) on the Gamma-centred periodic grid k = 2 pi (x/n1, y/n2, z/n3),
+    flat order k = x + n1*(y + n2*z). Returns (nk, n_orb, n_orb) complex128."""
+    z, y, x = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    kf = np.stack([x.ravel() / n1, y.ravel() / n2, z.ravel() / n3], axis=1)
+    n_orb = model["onsite"].shape[0]
+    H = np.zeros((kf.shape[0], n_orb, n_orb), np.complex128)
+    H[:, np.arange(n_orb), np.arange(n_orb)] = model["onsite"][None, :]
+    for R, t in zip(model["R"], model["t"]):
+        ph = np.exp(2j * np.pi * (kf @ R.astype(np.float64)))
+        H += ph[:, None, None] * t[None] + np.conj(ph)[:, None, None] * t.conj().T[None]
+    return H
+
+
+def eig(model: dict, n1: int, n2: int, n3: int, return_vectors: bool = False):
+    """FP64 dense diagonalisation at every grid point (LAPACK via numpy).
+    Returns eps (nk, nb) ascending and w (nk, nb, n_orb) with
+    w[k, n, s] = |V[k, s, n]|^2."""
+    H = hamiltonian(model, n1, n2, n3)
+    ev, V = np.linalg.eigh(H)
+    w = np.abs(np.transpose(V, (0, 2, 1))) ** 2
+    if return_vectors:
+        return ev, w, V
+    return ev, w
+
+
+# ---------------------------------------------------------------- DOS
+def dos(eps, w, n1, n2, n3, energies, mode="point", edges_hi=None, z_range=None,
+        nthreads: int = 1) -> np.ndarray:
+    """Orbital-resolved DOS, Eqs. (8)-(9).
+
+    eps (nk, nb), w (nk, nb, norb) in the natural layout. Point mode:
+    ``energies`` is any list of E values. Bin mode: either ``energies`` holds
+    nbins+1 ascending edges, or ``energies``/``edges_hi`` hold the lower and
+    upper edge of each bin. Returns (norb, npts).
+    """
+    lib = _load()
+    eps = _c64(eps)
+    w = _c64(w)
+    nk = n1 * n2 * n3
+    nb = eps.shape[1]
+    norb = w.shape[2]
+    assert eps.shape == (nk, nb) and w.shape == (nk, nb, norb)
+    if mode == "point":
+        ea = _c64(energies)
+        eb = ea
+        m = 0
+    elif mode == "bin":
+        if edges_hi is None:
+            e = _c64(energies)
+            ea = np.ascontiguousarray(e[:-1])
+            eb = np.ascontiguousarray(e[1:])
+        else:
+            ea = _c64(energies)
+            eb = _c64(edges_hi)
+        m = 1
+    else:
+        raise ValueError(mode)
+    npts = ea.shape[0]
+    out = np.zeros((norb, npts))
+    z0, z1 = (0, n3) if z_range is None else z_range
+    rc = lib.oracle_dos_range(n1, n2, n3, nb, norb, _p(eps), _p(w), m, npts, _p(ea), _p(eb),
+                              int(z0), int(z1), _p(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_dos_range failed ({rc})")
+    return out
+
+
+def dos_bin_grad(eps, w, n1, n2, n3, edges, g):
+    """Gradient of L = sum g * DOS_bin w.r.t. eps (nk, nb) and w (nk, nb, norb)."""
+    lib = _load()
+    eps = _c64(eps)
+    w = _c64(w)
+    e = _c64(edges)
+    ea = np.ascontiguousarray(e[:-1])
+    eb = np.ascontiguousarray(e[1:])
+    nk = n1 * n2 * n3
+    nb = eps.shape[1]
+    norb = w.shape[2]
+    g = _c64(g)
+    assert g.shape == (norb, ea.shape[0])
+    geps = np.zeros((nk, nb))
+    gw = np.zeros((nk, nb, norb))
+    rc = lib.oracle_dos_bin_grad(n1, n2, n3, nb, norb, _p(eps), _p(w), ea.shape[0], _p(ea),
+                                 _p(eb), _p(g), _p(geps), _p(gw))
+    if rc != 0:
+        raise RuntimeError(f"oracle_dos_bin_grad failed ({rc})")
+    return geps, gw
+
+
+# ---------------------------------------------------------------- eig backward
+def n_params(model: dict) -> int:
+    n_orb = model["onsite"].shape[0]
+    return n_orb + 2 * model["t"].shape[0] * n_orb * n_orb
+
+
+def model_to_params(model: dict) -> np.ndarray:
+    """Real parameter vector [onsite, Re t(R), Im t(R)]."""
+    return np.concatenate([model["onsite"], model["t"].real.ravel(), model["t"].imag.ravel()])
+
+
+def params_to_model(p: np.ndarray, like: dict) -> dict:
+    n_orb = like["onsite"].shape[0]
+    nR = like["t"].shape[0]
+    m = n_orb * n_orb * nR
+    t = (p[n_orb:n_orb + m] + 1j * p[n_orb + m:n_orb + 2 * m]).reshape(nR, n_orb, n_orb)
+    return {"onsite": p[:n_orb].copy(), "R": like["R"], "t": t}
+
+
+def eig_backward(model: dict, n1: int, n2: int, n3: int, geps, gw) -> np.ndarray:
+    """dL/dparams given dL/deps (nk, nb) and dL/dw (nk, nb, norb).
+
+    Per k: d eps_n = <n|dH|n> (Hellmann-Feynman) and
+    d c_n = sum_{m != n} c_m <m|dH|n> F_nm with F_nm = 1/(eps_n - eps_m),
+    regularised as d/(d^2 + ETA^2). With b_ns = |c_sn|^2 this gives
+    dL = Re sum_ij dH_ij Q_ij, Q = conj(V) (diag(geps) + 2 B) V^T,
+    B_mn = F_nm sum_s gw_ns conj(V_sn) V_sm. H(k) = D + sum_R t_R e^{ik.R} + h.c.
+    then gives dL/dRe t_R = Re sum_k Z, dL/dIm t_R = -Im sum_k Z,
+    Z = e^{ik.R} (Q + Q^H), and dL/dD_i = Re sum_k Q_ii.
+    """
+    H = hamiltonian(model, n1, n2, n3)
+    ev, V = np.linalg.eigh(H)
+    geps = _c64(geps)
+    gw = _c64(gw)
+    d = ev[:, :, None] - ev[:, None, :]          # d[k, n, m] = e_n - e_m
+    F = d / (d * d + ETA * ETA)
+    F[:, np.arange(d.shape[1]), np.arange(d.shape[1])] = 0.0
+    # A[k, n, m] = sum_s gw[k, n, s] conj(V[k, s, n]) V[k, s, m]
+    A = np.einsum("kns,ksn,ksm->knm", gw, np.conj(V), V)
+    B = np.transpose(A * F, (0, 2, 1))            # B[k, m, n] = A[k, n, m] F[k, n, m]
+    inner = 2.0 * B
+    idx = np.arange(d.shape[1])
+    inner[:, idx, idx] += geps
+    Q = np.einsum("kim,kmn,kjn->kij", np.conj(V), inner, V)
+    z, y, x = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    kf = np.stack([x.ravel() / n1, y.ravel() / n2, z.ravel() / n3], axis=1)
+    QQ = Q + np.conj(np.transpose(Q, (0, 2, 1)))
+    g_on = np.real(np.einsum("kii->i", Q))
+    g_re = []
+    g_im = []
+    for R in model["R"]:
+        ph = np.exp(2j * np.pi * (kf @ R.astype(np.float64)))
+        Zs = np.einsum("k,kij->ij", ph, QQ)
+        g_re.append(np.real(Zs))
+        g_im.append(-np.imag(Zs))
+    return np.concatenate([g_on, np.array(g_re).ravel(), np.array(g_im).ravel()])

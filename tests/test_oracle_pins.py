@@ -1,0 +1,447 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's formulas: the corner weights are checked
+against geometric integrals over the clipped tetrahedron and its iso-energy
+cross-section, Bloechl's closed-form tetrahedron DOS, finite differences,
+symmetries of the grid, the analytic simple-cubic DOS, Monte-Carlo sampling
+of the linear interpolant, and LAPACK.
+"""
+import itertools
+
+import numpy as np
+import pytest
+from scipy.spatial import ConvexHull
+
+import oracle
+import tbgen
+
+RNG = np.random.default_rng(12345)
+# Table I of the paper (corner labels), kept here independently of the oracle.
+TABLE_I = [(1, 2, 3, 6), (2, 3, 4, 6), (1, 3, 5, 6), (3, 4, 6, 8), (3, 5, 6, 7), (3, 6, 7, 8)]
+
+
+def corner_offset(c):
+    c -= 1
+    return np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1], float)
+
+
+# ---------------------------------------------------------------- geometry helpers
+STD = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0], [0, 0, 0]])  # simplex vertices
+
+
+def lam_of(P):
+    """Barycentric coordinates of points P (…,3) of the standard simplex."""
+    return np.concatenate([P, 1.0 - P.sum(-1, keepdims=True)], -1)
+
+
+def clipped_linear_integrals(e, E):
+    """Integral of lam_l over {eps < E} within the standard simplex (exact)."""
+    eps_v = np.asarray(e, float)
+    pts = [STD[i] for i in range(4) if eps_v[i] < E]
+    for i, j in itertools.combinations(range(4), 2):
+        a, b = eps_v[i], eps_v[j]
+        if (a - E) * (b - E) < 0:
+            t = (E - a) / (b - a)
+            pts.append(STD[i] + t * (STD[j] - STD[i]))
+    if len(pts) < 4:
+        return np.zeros(4)
+    P = np.array(pts)
+    try:
+        hull = ConvexHull(P)
+    except Exception:
+        return np.zeros(4)
+    c0 = P.mean(0)
+    tot = np.zeros(4)
+    for simp in hull.simplices:
+        A, B, C = P[simp]
+        vol = abs(np.dot(A - c0, np.cross(B - c0, C - c0))) / 6.0
+        cen = (A + B + C + c0) / 4.0
+        tot += vol * lam_of(cen)
+    return tot
+
+
+def cross_section_linear_integrals(e, E):
+    """Integral of lam_l delta(E - eps) over the standard simplex (exact)."""
+    eps_v = np.asarray(e, float)
+    pts = []
+    for i, j in itertools.combinations(range(4), 2):
+        a, b = eps_v[i], eps_v[j]
+        if (a - E) * (b - E) < 0:
+            t = (E - a) / (b - a)
+            pts.append(STD[i] + t * (STD[j] - STD[i]))
+    if len(pts) < 3:
+        return np.zeros(4)
+    P = np.array(pts)
+    c0 = P.mean(0)
+    grad = eps_v[:3] - eps_v[3]
+    nrm = grad / np.linalg.norm(grad)
+    ref = P[0] - c0
+    ref /= np.linalg.norm(ref)
+    other = np.cross(nrm, ref)
+    ang = np.arctan2((P - c0) @ other, (P - c0) @ ref)
+    P = P[np.argsort(ang)]
+    tot = np.zeros(4)
+    for q in range(len(P)):
+        A, B = P[q], P[(q + 1) % len(P)]
+        area = 0.5 * np.linalg.norm(np.cross(A - c0, B - c0))
+        tot += area * lam_of((A + B + c0) / 3.0)
+    return tot / np.linalg.norm(grad)
+
+
+def random_sorted_energies(rng, degenerate=None):
+    e = np.sort(rng.normal(0, 1, 4))
+    if degenerate == "12":
+        e[1] = e[0]
+    elif degenerate == "23":
+        e[2] = e[1]
+    elif degenerate == "34":
+        e[3] = e[2]
+    return e
+
+
+F = 1.0 / 24.0  # V_T/(4 V_G) for a 1x1x1 grid; any positive value works
+
+
+# ---------------------------------------------------------------- single tetrahedron
+@pytest.mark.parametrize("trial", range(12))
+def test_weights_equal_clipped_volume_integrals(trial):
+    rng = np.random.default_rng(100 + trial)
+    e = random_sorted_energies(rng)
+    for E in np.linspace(e[0] - 0.1, e[3] + 0.1, 23):
+        w, _ = oracle.corner_weights(e, E, F)
+        ref = 24.0 * F * clipped_linear_integrals(e, E)
+        np.testing.assert_allclose(w, ref, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("trial", range(12))
+def test_weight_derivatives_equal_cross_section_integrals(trial):
+    rng = np.random.default_rng(200 + trial)
+    e = random_sorted_energies(rng)
+    for E in np.linspace(e[0] + 1e-3, e[3] - 1e-3, 31):
+        if np.min(np.abs(E - e)) < 1e-6:
+            continue
+        _, dw = oracle.corner_weights(e, E, F)
+        ref = 24.0 * F * cross_section_linear_integrals(e, E)
+        np.testing.assert_allclose(dw, ref, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("trial", range(8))
+def test_weight_derivative_matches_finite_difference(trial):
+    rng = np.random.default_rng(300 + trial)
+    e = random_sorted_energies(rng)
+    h = 1e-6
+    for E in np.linspace(e[0] + 0.01, e[3] - 0.01, 40):
+        if np.min(np.abs(E - e)) < 10 * h:
+            continue
+        wp, _ = oracle.corner_weights(e, E + h, F)
+        wm, _ = oracle.corner_weights(e, E - h, F)
+        _, dw = oracle.corner_weights(e, E, F)
+        np.testing.assert_allclose(dw, (wp - wm) / (2 * h), rtol=1e-6, atol=1e-9)
+
+
+def bloechl_total_dos(e, E, vt_vg):
+    """Closed-form DOS of one tetrahedron (Bloechl et al., PRB 49, 16223)."""
+    E1, E2, E3, E4 = e
+    if E <= E1 or E >= E4:
+        return 0.0
+    if E <= E2:
+        return vt_vg * 3 * (E - E1) ** 2 / ((E2 - E1) * (E3 - E1) * (E4 - E1))
+    if E <= E3:
+        E21, E31, E41, E32, E42 = E2 - E1, E3 - E1, E4 - E1, E3 - E2, E4 - E2
+        return vt_vg / (E31 * E41) * (3 * E21 + 6 * (E - E2) - 3 * (E31 + E42) * (E - E2) ** 2 / (E32 * E42))
+    return vt_vg * 3 * (E4 - E) ** 2 / ((E4 - E1) * (E4 - E2) * (E4 - E3))
+
+
+@pytest.mark.parametrize("trial", range(10))
+def test_sum_of_corner_derivatives_is_bloechl_total_dos(trial):
+    rng = np.random.default_rng(400 + trial)
+    e = random_sorted_energies(rng)
+    for E in np.linspace(e[0] - 0.05, e[3] + 0.05, 57):
+        _, dw = oracle.corner_weights(e, E, F)
+        assert abs(dw.sum() - bloechl_total_dos(e, E, 4 * F)) < 1e-12 * max(1.0, abs(dw.sum()))
+
+
+@pytest.mark.parametrize("deg", [None, "12", "23", "34"])
+def test_continuity_and_limits(deg):
+    rng = np.random.default_rng(7)
+    for _ in range(10):
+        e = random_sorted_energies(rng, deg)
+        for Eb in e:
+            wl, dl = oracle.corner_weights(e, Eb - 1e-10, F)
+            wr, dr = oracle.corner_weights(e, Eb + 1e-10, F)
+            assert np.all(np.isfinite(wl)) and np.all(np.isfinite(dl))
+            np.testing.assert_allclose(wl, wr, atol=1e-8)
+        w0, d0 = oracle.corner_weights(e, e[0], F)
+        assert np.all(w0 == 0) and np.all(d0 == 0)
+        w4, d4 = oracle.corner_weights(e, e[3], F)
+        assert np.all(w4 == F) and np.all(d4 == 0)
+        # derivative continuity where both sides are in the interior
+        for Eb in (e[1], e[2]):
+            if e[0] < Eb < e[3] and len(set(e)) == 4:
+                _, dl = oracle.corner_weights(e, Eb - 1e-9, F)
+                _, dr = oracle.corner_weights(e, Eb + 1e-9, F)
+                np.testing.assert_allclose(dl, dr, rtol=1e-6, atol=1e-8)
+
+
+def test_all_degenerate_tetrahedron_is_a_step():
+    e = np.array([0.3, 0.3, 0.3, 0.3])
+    w, dw = oracle.corner_weights(e, 0.2, F)
+    assert np.all(w == 0)
+    w, dw = oracle.corner_weights(e, 0.4, F)
+    assert np.all(w == F) and np.all(dw == 0)
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_subdivision_invariance_linear_data(trial):
+    """Splitting a tetrahedron into 8 sub-tetrahedra with linearly interpolated
+    energies and orbital weights leaves the weighted DOS unchanged (the method
+    is exact for linear data)."""
+    rng = np.random.default_rng(500 + trial)
+    e = rng.normal(0, 1, 4)
+    b = rng.uniform(0, 1, 4)
+    V = np.eye(4)  # corners in barycentric coordinates
+    mid = {}
+    for i, j in itertools.combinations(range(4), 2):
+        mid[(i, j)] = 0.5 * (V[i] + V[j])
+    m = lambda i, j: mid[(min(i, j), max(i, j))]
+    subs = [
+        [V[0], m(0, 1), m(0, 2), m(0, 3)], [V[1], m(0, 1), m(1, 2), m(1, 3)],
+        [V[2], m(0, 2), m(1, 2), m(2, 3)], [V[3], m(0, 3), m(1, 3), m(2, 3)],
+        [m(0, 1), m(0, 2), m(0, 3), m(1, 3)], [m(0, 1), m(0, 2), m(1, 2), m(1, 3)],
+        [m(0, 2), m(0, 3), m(1, 3), m(2, 3)], [m(0, 2), m(1, 2), m(1, 3), m(2, 3)],
+    ]
+
+    def contrib(ev, bv, f, E):
+        order = np.argsort(ev, kind="stable")
+        _, dw = oracle.corner_weights(ev[order], E, f)
+        return float(np.dot(bv[order], dw)), np.array([
+            oracle.corner_weights(ev[order], E, f)[0]]).ravel(), order
+
+    for E in np.linspace(e.min() + 0.01, e.max() - 0.01, 17):
+        whole = contrib(e, b, F, E)[0]
+        parts = 0.0
+        for S in subs:
+            S = np.array(S)
+            parts += contrib(S @ e, S @ b, F / 8.0, E)[0]
+        assert abs(whole - parts) < 1e-11 * max(1.0, abs(whole))
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_weight_moments_match_finite_difference(trial):
+    rng = np.random.default_rng(600 + trial)
+    e = random_sorted_energies(rng)
+    h = 1e-6
+    for E in np.linspace(e[0] + 0.02, e[3] - 0.02, 15):
+        if np.min(np.abs(E - e)) < 1e-3:
+            continue
+        M = oracle.weight_moments(e, E, F)
+        for i in range(4):
+            ep = e.copy(); ep[i] += h
+            em = e.copy(); em[i] -= h
+            wp, _ = oracle.corner_weights(np.sort(ep), E, F)
+            wm, _ = oracle.corner_weights(np.sort(em), E, F)
+            np.testing.assert_allclose(-M[:, i], (wp - wm) / (2 * h), rtol=1e-5, atol=1e-9)
+        # shift invariance: sum_i dw_l/de_i = -dw_l/dE
+        _, dw = oracle.corner_weights(e, E, F)
+        np.testing.assert_allclose(M.sum(1), dw, rtol=1e-10, atol=1e-13)
+
+
+# ---------------------------------------------------------------- whole grids
+def test_table_one_partitions_the_cube():
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(0, 1, (4000, 3))
+    count = np.zeros(len(pts), int)
+    for tet in TABLE_I:
+        P = np.array([corner_offset(c) for c in tet])
+        T = (P[:3] - P[3]).T
+        lam = np.linalg.solve(T, (pts - P[3]).T).T
+        lam = np.concatenate([lam, 1 - lam.sum(1, keepdims=True)], 1)
+        count += np.all(lam >= -1e-12, axis=1)
+    assert np.all(count == 1)
+
+
+def small_problem(seed=3, n=(3, 2, 4), nb=2, norb=3):
+    n1, n2, n3 = n
+    rng = np.random.default_rng(seed)
+    nk = n1 * n2 * n3
+    eps = np.sort(rng.normal(0, 1, (nk, nb)), axis=1)
+    w = rng.uniform(0.05, 1, (nk, nb, norb))
+    w /= w.sum(2, keepdims=True)
+    return n1, n2, n3, eps, w
+
+
+def test_translation_invariance_of_grid_origin():
+    n1, n2, n3, eps, w = small_problem()
+    E = np.linspace(-2.5, 2.5, 41)
+    d0 = oracle.dos(eps, w, n1, n2, n3, E)
+    sh = lambda a: np.roll(a.reshape(n3, n2, n1, *a.shape[1:]), (1, -1, 2), axis=(0, 1, 2)).reshape(a.shape)
+    d1 = oracle.dos(sh(eps), sh(w), n1, n2, n3, E)
+    np.testing.assert_allclose(d0, d1, rtol=1e-12, atol=1e-14)
+
+
+def test_bin_mode_sum_rule_and_total():
+    model = tbgen.tb_model(5, n_orb=4)
+    n1 = n2 = n3 = 4
+    eps, w = oracle.eig(model, n1, n2, n3)
+    edges = np.linspace(eps.min() - 0.1, eps.max() + 0.1, 61)
+    d = oracle.dos(eps, w, n1, n2, n3, edges, mode="bin")
+    widths = np.diff(edges)
+    np.testing.assert_allclose((d * widths).sum(1), 1.0, rtol=0, atol=1e-12)
+    dtot = oracle.dos(eps, np.ones((eps.shape[0], eps.shape[1], 1)), n1, n2, n3, edges, mode="bin")
+    np.testing.assert_allclose(d.sum(0), dtot[0], rtol=1e-12, atol=1e-12)
+
+
+def test_point_mode_total_is_sum_over_orbitals():
+    model = tbgen.tb_model(6, n_orb=3)
+    eps, w = oracle.eig(model, 3, 3, 3)
+    E = np.linspace(eps.min(), eps.max(), 37)
+    d = oracle.dos(eps, w, 3, 3, 3, E)
+    dtot = oracle.dos(eps, np.ones((eps.shape[0], eps.shape[1], 1)), 3, 3, 3, E)
+    np.testing.assert_allclose(d.sum(0), dtot[0], rtol=1e-11, atol=1e-12)
+
+
+def test_thread_count_does_not_change_result_beyond_rounding():
+    n1, n2, n3, eps, w = small_problem(n=(4, 4, 6))
+    E = np.linspace(-2, 2, 33)
+    d1 = oracle.dos(eps, w, n1, n2, n3, E, nthreads=1)
+    d3 = oracle.dos(eps, w, n1, n2, n3, E, nthreads=3)
+    np.testing.assert_allclose(d1, d3, rtol=1e-12, atol=1e-15)
+
+
+def test_z_range_partition_adds_up():
+    n1, n2, n3, eps, w = small_problem(n=(3, 3, 5))
+    E = np.linspace(-2, 2, 21)
+    full = oracle.dos(eps, w, n1, n2, n3, E)
+    parts = sum(oracle.dos(eps, w, n1, n2, n3, E, z_range=(a, b)) for a, b in [(0, 2), (2, 3), (3, 5)])
+    np.testing.assert_allclose(full, parts, rtol=1e-12, atol=1e-15)
+
+
+def test_monte_carlo_histogram_of_linear_interpolant():
+    """Bin DOS equals the histogram of the piecewise-linear interpolant sampled
+    uniformly over each cube (tetrahedron located from Table I)."""
+    n1, n2, n3, eps, w = small_problem(seed=11, n=(2, 2, 2), nb=1, norb=2)
+    rng = np.random.default_rng(99)
+    edges = np.linspace(eps.min() - 0.05, eps.max() + 0.05, 13)
+    hist = np.zeros((2, len(edges) - 1))
+    tets = [np.array([corner_offset(c) for c in tet]) for tet in TABLE_I]
+    inv = [np.linalg.inv((P[:3] - P[3]).T) for P in tets]
+    ns = 400_000
+    for z in range(n3):
+        for y in range(n2):
+            for x in range(n1):
+                pts = rng.uniform(0, 1, (ns, 3))
+                for P, Ti, tet in zip(tets, inv, TABLE_I):
+                    lam = (Ti @ (pts - P[3]).T).T
+                    lam = np.concatenate([lam, 1 - lam.sum(1, keepdims=True)], 1)
+                    inside = np.all(lam >= 0, axis=1)
+                    L = lam[inside]
+                    ks = []
+                    for c in tet:
+                        o = corner_offset(c).astype(int)
+                        ks.append(((x + o[0]) % n1) + n1 * (((y + o[1]) % n2) + n2 * ((z + o[2]) % n3)))
+                    ev = L @ eps[ks, 0]
+                    for s in range(2):
+                        bv = L @ w[ks, 0, s]
+                        h, _ = np.histogram(ev, bins=edges, weights=bv)
+                        hist[s] += h
+    hist /= (ns * n1 * n2 * n3) * np.diff(edges)
+    d = oracle.dos(eps, w, n1, n2, n3, edges, mode="bin")
+    assert np.max(np.abs(hist - d)) < 0.02 * np.max(d)
+
+
+def sc_exact_dos(E, t=1.0):
+    """Exact DOS of eps = -2t(cos kx + cos ky + cos kz), from the square-lattice
+    DOS (complete elliptic integral) averaged over k_z."""
+    from scipy.integrate import quad
+    from scipy.special import ellipk
+
+    def rho2(e):
+        if abs(e) >= 4 * t:
+            return 0.0
+        m = 1.0 - (e / (4 * t)) ** 2
+        return ellipk(m) / (2 * np.pi ** 2 * t)
+
+    val, _ = quad(lambda kz: rho2(E + 2 * t * np.cos(kz)), 0, np.pi, limit=200)
+    return val / np.pi
+
+
+def sc_eps(n):
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    k = 2 * np.pi / n
+    return (-2 * (np.cos(k * x) + np.cos(k * y) + np.cos(k * z))).reshape(-1, 1)
+
+
+def test_simple_cubic_particle_hole_symmetry():
+    n = 8
+    eps = sc_eps(n)
+    w = np.ones((n ** 3, 1, 1))
+    E = np.linspace(-6.5, 6.5, 131)
+    d = oracle.dos(eps, w, n, n, n, E)
+    np.testing.assert_allclose(d[0], d[0][::-1], rtol=1e-10, atol=1e-12)
+
+
+def test_simple_cubic_converges_to_analytic_dos():
+    E = np.array([-5.0, -3.0, -1.0, 1.0, 3.0, 5.0])
+    exact = np.array([sc_exact_dos(x) for x in E])
+    errs = []
+    for n in (12, 24):
+        eps = sc_eps(n)
+        d = oracle.dos(eps, np.ones((n ** 3, 1, 1)), n, n, n, E)[0]
+        errs.append(np.max(np.abs(d - exact)))
+    assert errs[1] < 0.01 * exact.max()
+    assert errs[0] / errs[1] > 2.5  # second order in the grid spacing
+
+
+def test_eig_matches_simple_cubic_dispersion_and_is_orthonormal():
+    eps, w, V = oracle.eig(tbgen.sc_model(), 5, 5, 5, return_vectors=True)
+    np.testing.assert_allclose(eps, sc_eps(5), atol=1e-13)
+    model = tbgen.tb_model(2)
+    H = oracle.hamiltonian(model, 3, 2, 2)
+    ev, w, V = oracle.eig(model, 3, 2, 2, return_vectors=True)
+    np.testing.assert_allclose(H @ V, V * ev[:, None, :], atol=1e-12)
+    np.testing.assert_allclose(w.sum(1), 1.0, atol=1e-12)   # sum over bands
+    np.testing.assert_allclose(w.sum(2), 1.0, atol=1e-12)   # sum over orbitals
+    np.testing.assert_allclose(H, np.conj(np.transpose(H, (0, 2, 1))), atol=0)
+
+
+def test_bin_gradient_matches_finite_difference():
+    n1, n2, n3, eps, w = small_problem(seed=21, n=(2, 2, 3), nb=2, norb=2)
+    edges = np.linspace(eps.min() - 0.2, eps.max() + 0.2, 9)
+    g = np.random.default_rng(4).normal(0, 1, (2, 8))
+    geps, gw = oracle.dos_bin_grad(eps, w, n1, n2, n3, edges, g)
+    L = lambda e_, w_: float((g * oracle.dos(e_, w_, n1, n2, n3, edges, mode="bin")).sum())
+    h = 1e-6
+    for idx in [(0, 0), (3, 1), (7, 0), (11, 1)]:
+        ep = eps.copy(); ep[idx] += h
+        em = eps.copy(); em[idx] -= h
+        fd = (L(ep, w) - L(em, w)) / (2 * h)
+        assert abs(fd - geps[idx]) < 1e-6 * max(1.0, abs(fd))
+    for idx in [(0, 0, 0), (5, 1, 1), (9, 0, 1)]:
+        wp = w.copy(); wp[idx] += h
+        wm = w.copy(); wm[idx] -= h
+        fd = (L(eps, wp) - L(eps, wm)) / (2 * h)
+        assert abs(fd - gw[idx]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_eig_backward_matches_finite_difference_of_fp64_chain():
+    model = tbgen.tb_model(8, n_orb=4)
+    n1, n2, n3 = 3, 3, 2
+    eps, w = oracle.eig(model, n1, n2, n3)
+    edges = np.linspace(eps.min() - 0.3, eps.max() + 0.3, 11)
+    g = np.random.default_rng(5).normal(0, 1, (4, 10))
+
+    def loss(p):
+        m = oracle.params_to_model(p, model)
+        e_, w_ = oracle.eig(m, n1, n2, n3)
+        return float((g * oracle.dos(e_, w_, n1, n2, n3, edges, mode="bin")).sum())
+
+    geps, gw = oracle.dos_bin_grad(eps, w, n1, n2, n3, edges, g)
+    grad = oracle.eig_backward(model, n1, n2, n3, geps, gw)
+    p0 = oracle.model_to_params(model)
+    assert grad.shape == p0.shape
+    h = 1e-6
+    for i in [0, 3, 5, 20, 41, 77, 130, 200, 227]:
+        pp = p0.copy(); pp[i] += h
+        pm = p0.copy(); pm[i] -= h
+        fd = (loss(pp) - loss(pm)) / (2 * h)
+        assert abs(fd - grad[i]) < 2e-5 * max(1.0, abs(fd)), (i, fd, grad[i])
