@@ -1,0 +1,362 @@
+"""Benchmark of the linear tetrahedron orbital-resolved DOS on GB300.
+
+One step = the whole hot path on one synthetic tight-binding model: H(k) and
+the batched Jacobi eigensolve on the GPU (tetra_eig), then the orbital-resolved
+DOS by the linear tetrahedron method (tetra_dos). Default workload: seeded
+8-orbital tetragonal model, 256^3 k-grid (100.7M tetrahedra), 8 bands,
+8 orbitals, 4000 energies on [eps_min - 0.1, eps_max + 0.1], FP32 weights,
+point mode. Inputs (4.9 GB of eigen-data) are larger than L2.
+
+Metric: tetrahedron x band x energy updates per second, counting every
+(tetrahedron, band, energy) triple the method defines (the dense count the
+paper's thread-per-energy kernel evaluates); the in-window count is reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank integrates its own seeded model (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tetrahedron*band*omega updates/sec"
+UNIT = "updates/s"
+# FP32 lanes per SM on GB300 (4 partitions x 32) and the SM count
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 FMA-pipe instructions: per in-window (tetra, band, energy)
+# triple with n_orb = 8, and per (tetra, band) item (sort, window, reciprocals)
+OPS_PER_TRIPLE = 44
+OPS_PER_ITEM = 40
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--n-omega", type=int, default=4000)
+    ap.add_argument("--weight-dtype", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--mode", default="point", choices=["point", "bin"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip e2e and extra measurements")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def model_arrays(model):
+    p = np.concatenate([model["onsite"], model["t"].real.ravel(), model["t"].imag.ravel()])
+    return p.astype(np.float32), model["R"].astype(np.int32)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def in_window_count(torch, eps, n, nb, omega, mode):
+    """Exact number of (tetra, band, energy) triples with the energy strictly
+    inside (E1, E4) (point mode) or the bin overlapping it (bin mode)."""
+    table = [(0, 1, 2, 5), (1, 2, 3, 5), (0, 2, 4, 5), (2, 3, 5, 7), (2, 4, 5, 6), (2, 5, 6, 7)]
+    om = omega.double()
+    total = 0
+    for z in range(n):
+        planes = eps[z:z + 2, :, :, :nb].double()  # (2, n+1, n+1, nb)
+        for t in table:
+            cs = []
+            for c in t:
+                dx, dy, dz = c & 1, (c >> 1) & 1, (c >> 2) & 1
+                cs.append(planes[dz, dy:dy + n, dx:dx + n, :])
+            st = torch.stack(cs, 0)
+            e1 = st.min(0).values.reshape(-1)
+            e4 = st.max(0).values.reshape(-1)
+            if mode == "point":
+                lo = torch.searchsorted(om, e1, right=True)
+                hi = torch.searchsorted(om, e4, right=False)
+            else:
+                lo = torch.searchsorted(om, e1, right=True) - 1
+                hi = torch.searchsorted(om, e4, right=False)
+                lo = lo.clamp(min=0)
+                hi = hi.clamp(max=om.numel() - 1)
+            total += int((hi - lo).clamp(min=0).sum().item())
+    return total
+
+
+def cpu_baseline(n, n_omega, seed=0, planes=1, threads=None):
+    """The FP64 oracle on the host cores over a bounded sample of the same
+    workload: `planes` cube planes (n x n x planes cubes) of the n^3 grid, all
+    bands and all energies, eigen-data from the oracle's own eigensolver."""
+    import oracle
+    import tbgen
+    threads = threads or os.cpu_count() or 1
+    model = tbgen.tb_model(seed)
+    # k-points of planes z = 0..planes of the n^3 grid
+    zs = np.arange(planes + 1)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    H = []
+    for z in zs:
+        kf = np.stack([x.ravel() / n, y.ravel() / n, np.full(x.size, z / n)], 1)
+        Hz = np.zeros((kf.shape[0], 8, 8), np.complex128)
+        Hz[:, np.arange(8), np.arange(8)] = model["onsite"]
+        for R, t in zip(model["R"], model["t"]):
+            ph = np.exp(2j * np.pi * (kf @ R.astype(float)))
+            Hz += ph[:, None, None] * t[None] + np.conj(ph)[:, None, None] * t.conj().T[None]
+        H.append(Hz)
+    ev, V = np.linalg.eigh(np.concatenate(H))
+    w = np.abs(np.transpose(V, (0, 2, 1))) ** 2
+    e_lo, e_hi = ev.min() - 0.1, ev.max() + 0.1
+    omega = np.linspace(e_lo, e_hi, n_omega).astype(np.float32).astype(np.float64)
+    n3 = planes + 1
+    t0 = time.perf_counter()
+    oracle.dos(ev, w, n, n, n3, omega, z_range=(0, planes), nthreads=threads)
+    dt = time.perf_counter() - t0
+    updates = n * n * planes * 6 * 8 * n_omega
+    return {"value": updates / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{planes} cube plane(s) of the {n}^3 grid ({n * n * planes * 6} tetrahedra) "
+                      f"x 8 bands x {n_omega} energies, FP64, dense over energies",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    # bounded sample per step: a quarter plane keeps K+W steps within minutes
+    import oracle  # noqa: F401
+    res = []
+    for i in range(warm + steps):
+        r = cpu_baseline(args.grid, args.n_omega, planes=1)
+        if i >= warm:
+            res.append(r)
+    v = statistics.mean(r["value"] for r in res)
+    cb = dict(res[0])
+    cb["value"] = v
+    cb.pop("seconds", None)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+            "warmup": warm, "ms_per_step": statistics.mean(r["seconds"] for r in res) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"tb8_{args.grid}cube_{args.n_omega}w_{args.mode}",
+                       "grid": args.grid, "n_omega": args.n_omega},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import paper_1710_10789_gb300 as T
+    import tbgen
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T.build()
+    n, nw = args.grid, args.n_omega
+    model = tbgen.tb_model(rank, n_orb=8)
+    p_np, R_np = model_arrays(model)
+    params = torch.from_numpy(p_np).to(dev)
+    R = torch.from_numpy(R_np).to(dev)
+    plan = T.Plan(n, n, n, 8, 8, nw, mode=args.mode, weight_dtype=args.weight_dtype, device=local)
+    eps, w = plan.empty_inputs()
+    ws = plan.workspace()
+    stream = torch.cuda.current_stream()
+    # energy window from the eigenvalues the DOS kernel consumes (fixed before timing)
+    plan.eig(params, R, eps, w)
+    torch.cuda.synchronize()
+    emin = float(eps[..., :8].min())
+    emax = float(eps[..., :8].max())
+    if args.mode == "point":
+        omega = torch.from_numpy(tbgen.uniform_grid(emin - 0.1, emax + 0.1, nw)).to(dev)
+    else:
+        omega = torch.from_numpy(tbgen.bin_edges(emin - 0.1, emax + 0.1, nw)).to(dev)
+    dos = torch.empty((8, nw), dtype=torch.float32, device=dev)
+
+    def step():
+        plan.eig(params, R, eps, w)
+        plan.dos(eps, w, omega, out=dos)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert plan.status() == T.TETRA_OK
+    # timed region: K steps, per-kernel events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            plan.eig(params, R, eps, w)
+            ev[i][1].record(stream)
+            plan.dos(eps, w, omega, out=dos)
+            ev[i][2].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    eig_ms = statistics.mean(a.elapsed_time(b) for a, b, c in ev)
+    dos_ms = statistics.mean(b.elapsed_time(c) for a, b, c in ev)
+    ms_step = total_ms / args.steps
+    n_tet = 6 * n ** 3
+    dense = n_tet * 8 * nw
+    value = dense * world / (ms_step * 1e-3)
+    if rank != 0:
+        return
+    triples = in_window_count(torch, eps, n, 8, omega, args.mode)
+    clocks = clk.summary()
+    mp = {}
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = float(mp.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    alg_flops = 2.0 * (OPS_PER_TRIPLE * triples + OPS_PER_ITEM * n_tet * 8)
+    achieved = alg_flops / (dos_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "tetra_dos_fwd_kernel", "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "traffic": None,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                           "(sm_max_mhz of measured MEASURED_PEAKS.json)",
+            "algorithmic": f"{OPS_PER_TRIPLE} FMA-pipe ops x {triples} in-window triples + "
+                           f"{OPS_PER_ITEM} x {n_tet * 8} tetra-bands"}
+    # end to end through the public API: host model in, host DOS out
+    e2e = None
+    if not args.quick:
+        p_host = torch.from_numpy(p_np).pin_memory()
+        R_host = torch.from_numpy(R_np).pin_memory()
+        d_host = torch.empty((8, nw), dtype=torch.float32).pin_memory()
+        p_dev = torch.empty_like(params)
+        R_dev = torch.empty_like(R)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            p_dev.copy_(p_host, non_blocking=True)
+            R_dev.copy_(R_host, non_blocking=True)
+            plan.eig(p_dev, R_dev, eps, w)
+            plan.dos(eps, w, omega, out=dos)
+            d_host.copy_(dos, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        e2e = {"value": dense / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(p_host.numel() * 4 + R_host.numel() * 4),
+               "d2h_bytes_per_step": int(d_host.numel() * 4), "ms_per_step": e2e_ms}
+    cb = None
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline(n, nw, seed=0, planes=1)
+        cb.pop("seconds", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"tb8_{n}cube_{nw}w_{args.mode}_{args.weight_dtype}",
+                   "model": "seeded 8-orbital tetragonal tight binding", "grid": [n, n, n],
+                   "tetrahedra": n_tet, "n_bands": 8, "n_orb": 8, "n_omega": nw,
+                   "mode": args.mode, "weight_dtype": args.weight_dtype,
+                   "l2": "inputs larger than L2 (eigen-data %.1f GB)" % (
+                       (eps.numel() * 4 + w.numel() * w.element_size()) / 1e9),
+                   "parallelism": f"{world} independent model(s), one per GPU"},
+        "step": {"eig_ms": eig_ms, "dos_ms": dos_ms},
+        "in_window_updates_per_s": triples / (dos_ms * 1e-3),
+        "dense_updates_per_s_dos_only": dense / (dos_ms * 1e-3),
+        "in_window_triples": triples,
+        "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": 3 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * tetra.h - C ABI of libtetra, a GB300 (sm_103a) implementation of the linear
+ * tetrahedron method for the orbital-resolved density of states
+ * (D. Guterding, H. O. Jeschke, "An efficient GPU algorithm for
+ * tetrahedron-based Brillouin-zone integration", arXiv:1710.10789).
+ *
+ * General conventions
+ *  - Every entry point returns a tetra_status_t; nothing is thrown across the
+ *    ABI. Argument errors are reported synchronously, before any work is
+ *    enqueued. Work is enqueued on the given CUDA stream and runs
+ *    asynchronously; errors raised on the device (a wait that timed out, a
+ *    value outside the representable range) are recorded in the workspace and
+ *    returned by tetra_workspace_status().
+ *  - All array arguments are DEVICE pointers owned by the caller, except where
+ *    a parameter says "host". The library never frees caller memory. Outputs
+ *    are overwritten, never accumulated into.
+ *  - Results are deterministic: the same plan, inputs and workspace size give
+ *    bit-identical outputs. The DOS is accumulated in exact 64-bit fixed point,
+ *    so it is also independent of the launch shape.
+ *
+ * k-grid and the padded point-major layout ("tetra layout")
+ *  - The k-grid is periodic and Gamma-centred with n1 x n2 x n3 points,
+ *    k = 2 pi (x/n1, y/n2, z/n3) in reciprocal-lattice units (Sec. III.A uses
+ *    N x N x 10 grids). Every point is the origin of one elemental cube, which
+ *    is split into the six tetrahedra of Table I around its 3-6 diagonal; cube
+ *    corner label c = 1 + dx + 2 dy + 4 dz for the offset (dx, dy, dz).
+ *  - Band energies and orbital weights are stored per grid point, with one
+ *    periodic halo plane in each direction: P = (n1+1)(n2+1)(n3+1) points,
+ *    point index p = x + (n1+1) (y + (n2+1) z) for x <= n1, y <= n2, z <= n3,
+ *    holding the data of k-point (x mod n1, y mod n2, z mod n3).
+ *      eps: float, eps[p * eps_stride + n]                  (band n)
+ *      w  : F32/F16/BF16, w[p * w_stride + n * n_orb + s]  (band n, orbital s)
+ *    with the strides reported by tetra_layout(). Both arrays must be 16-byte
+ *    aligned. Bands are sorted ascending at each point (Sec. II.A diagonalises
+ *    H(k) point by point), and w = |a^s_n(k)|^2 of Eq. (3).
+ */
+#ifndef TETRA_H
+#define TETRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TETRA_OK = 0,
+    TETRA_EINVAL = 1,        /* bad argument (null pointer, size, alignment)      */
+    TETRA_EUNSUPPORTED = 2,  /* valid request this build does not support         */
+    TETRA_ECUDA = 3,         /* a CUDA runtime call failed                        */
+    TETRA_ENOMEM = 4,        /* workspace too small / allocation failed           */
+    TETRA_ETIMEOUT = 5,      /* a device-side wait hit its iteration limit        */
+    TETRA_ERANGE = 6         /* a contribution exceeded the fixed-point range     */
+} tetra_status_t;
+
+enum { TETRA_POINT = 0, TETRA_BIN = 1 };
+enum { TETRA_F32 = 0, TETRA_F16 = 1, TETRA_BF16 = 2 };
+
+/* Problem description of one DOS evaluation. */
+typedef struct {
+    int n1, n2, n3;     /* k-grid size, each >= 1                                   */
+    int n_bands;        /* bands per k-point, 1..64                                 */
+    int n_orb;          /* orbitals, 1..16 (Sec. III.B: up to 16 orbitals)          */
+    int n_omega;        /* energies (TETRA_POINT) or bins (TETRA_BIN), >= 1         */
+    int mode;           /* TETRA_POINT: rho_s(E) at energies, Eq. (9);
+                           TETRA_BIN: bin averages of rho_s over consecutive edges */
+    int weight_dtype;   /* storage type of w: TETRA_F32, TETRA_F16, TETRA_BF16      */
+    int z_begin, z_end; /* cube planes [z_begin, z_end) to integrate (a k-slab, for
+                           splitting one grid over several calls or devices);
+                           0, 0 means the whole grid                                */
+} tetra_desc_t;
+
+/* Element strides of the tetra layout for a plan. */
+typedef struct {
+    int nx, ny, nz;       /* padded extents n1+1, n2+1, n3+1                        */
+    int eps_stride;       /* floats per point in eps                                */
+    int w_stride;         /* elements per point in w                                */
+    size_t eps_elems;     /* total floats of eps  = nx*ny*nz*eps_stride             */
+    size_t w_elems;       /* total elements of w  = nx*ny*nz*w_stride               */
+} tetra_layout_t;
+
+typedef struct tetra_plan_s *tetra_plan_t;
+
+/* Creates a plan for desc on CUDA device `device` (host call; reads device
+ * properties, picks the box shape and grid of the kernels). The plan owns only
+ * host memory. Returns TETRA_EINVAL for an invalid desc. */
+tetra_status_t tetra_plan(tetra_plan_t *plan, const tetra_desc_t *desc, int device);
+
+/* Destroys a plan (host memory only). Safe on NULL. */
+tetra_status_t tetra_plan_destroy(tetra_plan_t plan);
+
+/* Layout strides the plan expects (host call). */
+tetra_status_t tetra_layout(tetra_plan_t plan, tetra_layout_t *layout);
+
+/* Bytes of device workspace tetra_dos / tetra_dos_backward need (host call). */
+size_t tetra_workspace_bytes(tetra_plan_t plan);
+
+/* Orbital-resolved DOS by the linear tetrahedron method (Sec. II.C, Eqs. (8)-(9)).
+ *   eps, w : band energies and orbital weights in the tetra layout.
+ *   omega  : TETRA_POINT: n_omega ascending energies E_i.
+ *            TETRA_BIN:   n_omega + 1 ascending bin edges.
+ *            Any ascending grid is correct; equidistant grids (Sec. III.A) are
+ *            fastest.
+ *   dos    : [n_orb][n_omega] float, overwritten.
+ *            TETRA_POINT: dos[s][i] = sum_{T,n} sum_l b_{n,l,s} dw_l/dE (E_i).
+ *            TETRA_BIN:   dos[s][i] = sum_{T,n} sum_l b_{n,l,s}
+ *                           [w_l(e_{i+1}) - w_l(e_i)] / (e_{i+1} - e_i).
+ *            Normalised per spin and orbital: with unitary weights the bin
+ *            DOS of each orbital integrates to 1.
+ *   ws     : device workspace of at least tetra_workspace_bytes(plan) bytes,
+ *            16-byte aligned; contents on entry are ignored.
+ * Returns TETRA_EINVAL for null/misaligned pointers or ws_bytes too small. */
+tetra_status_t tetra_dos(tetra_plan_t plan, const float *eps, const void *w,
+                         const float *omega, float *dos, void *ws, size_t ws_bytes,
+                         cudaStream_t stream);
+
+/* Adjoint of tetra_dos in TETRA_BIN mode (not in the paper; the derivative of
+ * its bin-averaged DOS). Given grad_dos = dL/d dos [n_orb][n_omega], writes
+ *   grad_eps = dL/d eps (float, tetra layout, eps_stride)
+ *   grad_w   = dL/d w   (float, tetra layout with w_stride; F32 even when w
+ *                        is stored in F16/BF16)
+ * Interior points receive the full derivative with respect to the value of
+ * that k-point; halo points (x == n1 or y == n2 or z == n3) are set to 0.
+ * Returns TETRA_EUNSUPPORTED for a TETRA_POINT plan. */
+tetra_status_t tetra_dos_backward(tetra_plan_t plan, const float *eps, const void *w,
+                                  const float *omega, const float *grad_dos,
+                                  float *grad_eps, float *grad_w, void *ws,
+                                  size_t ws_bytes, cudaStream_t stream);
+
+/* Tight-binding model in device memory, the hopping form of Eq. (1):
+ *   H(k) = diag(onsite) + sum_r [ t_r e^{i k.R_r} + t_r^dagger e^{-i k.R_r} ].
+ * params: onsite[n_orb] followed by Re t[n_R][n_orb][n_orb] and then
+ *         Im t[n_R][n_orb][n_orb] (float; row index = first orbital index).
+ * R: int[n_R][3] lattice vectors. */
+typedef struct {
+    int n_orb;            /* 1..8 for tetra_eig                                     */
+    int n_R;              /* number of independent lattice vectors, 0..32           */
+    const float *params;  /* device, n_orb + 2 n_R n_orb^2 floats                   */
+    const int *R;         /* device, 3 n_R ints                                     */
+} tetra_model_t;
+
+/* Band energies and orbital weights of a tight-binding model on the plan's
+ * grid (Sec. II.A: diagonalisation of H(k) point by point), written directly
+ * in the tetra layout. A batched cyclic Jacobi eigensolver on the GPU; bands
+ * ascending, w[n][s] = |V_{s n}|^2 stored in the plan's weight_dtype.
+ * Requires plan n_bands == model n_orb <= 8. Halo points are written too. */
+tetra_status_t tetra_eig(tetra_plan_t plan, const tetra_model_t *model, float *eps, void *w,
+                         cudaStream_t stream);
+
+/* Derivative of a loss through tetra_eig to the model parameters (not in the
+ * paper): given dL/d eps and dL/d w in the tetra layout (float; halo entries
+ * ignored), writes grad_params (same packing as model->params, float).
+ * Eigenvector derivatives use F_nm = d/(d^2 + eta^2), d = e_n - e_m, in FP64,
+ * eta = 1e-8 eV. Needs tetra_eig_workspace_bytes(plan) bytes of workspace. */
+tetra_status_t tetra_eig_backward(tetra_plan_t plan, const tetra_model_t *model,
+                                  const float *grad_eps, const float *grad_w,
+                                  float *grad_params, void *ws, size_t ws_bytes,
+                                  cudaStream_t stream);
+size_t tetra_eig_workspace_bytes(tetra_plan_t plan, int n_R);
+
+/* Device-side status recorded in a workspace by the last call that used it
+ * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. */
+tetra_status_t tetra_workspace_status(const void *ws, cudaStream_t stream);
+
+/* Human-readable name of a status. */
+const char *tetra_strerror(tetra_status_t status);
+
+/* Library version, e.g. "0.1.0". */
+const char *tetra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TETRA_H */

@@ -1,0 +1,285 @@
+"""Python binding of libtetra (GB300 / sm_103a linear tetrahedron DOS).
+
+The functions named ``tetra_*`` mirror the C ABI in ``include/tetra.h``
+one-to-one (argument marshalling through ctypes; pointers are integers). The
+``Plan`` class and the autograd functions in ``autograd`` add PyTorch tensor
+convenience on top: PyTorch provides device memory and streams only, every
+step of the method runs in the library's CUDA kernels.
+
+The library must be built first (``paper_1710_10789_gb300.build()`` or
+``python -c "import __graft_entry__ as g; g.build()"``); without it every call
+raises ``TetraError`` — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+__all__ = [
+    "TETRA_OK", "TETRA_POINT", "TETRA_BIN", "TETRA_F32", "TETRA_F16", "TETRA_BF16",
+    "TetraError", "TetraDesc", "TetraLayout", "TetraModel", "build", "lib", "lib_path",
+    "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
+    "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
+    "tetra_workspace_status", "tetra_strerror", "tetra_version", "Plan", "EXPORTED_SYMBOLS",
+]
+
+TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
+TETRA_POINT, TETRA_BIN = 0, 1
+TETRA_F32, TETRA_F16, TETRA_BF16 = 0, 1, 2
+_DTYPES = {"f32": TETRA_F32, "f16": TETRA_F16, "bf16": TETRA_BF16}
+_MODES = {"point": TETRA_POINT, "bin": TETRA_BIN}
+
+#: Every extern "C" symbol declared in include/tetra.h.
+EXPORTED_SYMBOLS = (
+    "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
+    "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
+    "tetra_workspace_status", "tetra_strerror", "tetra_version",
+)
+
+
+class TetraError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = tetra_strerror(status) if _LIB is not None else f"status {status}"
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+class TetraDesc(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+                ("n_bands", ctypes.c_int), ("n_orb", ctypes.c_int), ("n_omega", ctypes.c_int),
+                ("mode", ctypes.c_int), ("weight_dtype", ctypes.c_int),
+                ("z_begin", ctypes.c_int), ("z_end", ctypes.c_int)]
+
+
+class TetraLayout(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("eps_stride", ctypes.c_int), ("w_stride", ctypes.c_int),
+                ("eps_elems", ctypes.c_size_t), ("w_elems", ctypes.c_size_t)]
+
+
+class TetraModel(ctypes.Structure):
+    _fields_ = [("n_orb", ctypes.c_int), ("n_R", ctypes.c_int),
+                ("params", ctypes.c_void_p), ("R", ctypes.c_void_p)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile libtetra.so in-tree for sm_103a."""
+    return _build.build(force=force)
+
+
+def lib_path() -> str:
+    return _build.LIBPATH
+
+
+def lib():
+    """The loaded libtetra (raises if it was not built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(_build.LIBPATH):
+                raise TetraError(TETRA_ECUDA, f"libtetra.so missing at {_build.LIBPATH}; "
+                                 "build it with paper_1710_10789_gb300.build()")
+            L = ctypes.CDLL(_build.LIBPATH)
+            vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            L.tetra_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(TetraDesc), i]
+            L.tetra_plan_destroy.argtypes = [vp]
+            L.tetra_layout.argtypes = [vp, ctypes.POINTER(TetraLayout)]
+            L.tetra_workspace_bytes.argtypes = [vp]
+            L.tetra_workspace_bytes.restype = sz
+            L.tetra_dos.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+            L.tetra_dos_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+            L.tetra_eig.argtypes = [vp, ctypes.POINTER(TetraModel), vp, vp, vp]
+            L.tetra_eig_backward.argtypes = [vp, ctypes.POINTER(TetraModel), vp, vp, vp, vp, sz, vp]
+            L.tetra_eig_workspace_bytes.argtypes = [vp, i]
+            L.tetra_eig_workspace_bytes.restype = sz
+            L.tetra_workspace_status.argtypes = [vp, vp]
+            L.tetra_strerror.argtypes = [i]
+            L.tetra_strerror.restype = ctypes.c_char_p
+            L.tetra_version.restype = ctypes.c_char_p
+            for name in ("tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_dos",
+                         "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
+                         "tetra_workspace_status"):
+                getattr(L, name).restype = i
+            _LIB = L
+    return _LIB
+
+
+def _check(st: int, what: str):
+    if st != TETRA_OK:
+        raise TetraError(st, what)
+
+
+# ------------------------------------------------------------------ C ABI mirror
+def tetra_plan(desc: TetraDesc, device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tetra_plan(ctypes.byref(h), ctypes.byref(desc), int(device)), "tetra_plan")
+    return h.value
+
+
+def tetra_plan_destroy(plan: int) -> int:
+    return lib().tetra_plan_destroy(plan)
+
+
+def tetra_layout(plan: int) -> TetraLayout:
+    L = TetraLayout()
+    _check(lib().tetra_layout(plan, ctypes.byref(L)), "tetra_layout")
+    return L
+
+
+def tetra_workspace_bytes(plan: int) -> int:
+    return int(lib().tetra_workspace_bytes(plan))
+
+
+def tetra_dos(plan, eps, w, omega, dos, ws, ws_bytes, stream) -> int:
+    return lib().tetra_dos(plan, eps, w, omega, dos, ws, ws_bytes, stream)
+
+
+def tetra_dos_backward(plan, eps, w, omega, grad_dos, grad_eps, grad_w, ws, ws_bytes, stream) -> int:
+    return lib().tetra_dos_backward(plan, eps, w, omega, grad_dos, grad_eps, grad_w, ws, ws_bytes,
+                                    stream)
+
+
+def tetra_eig(plan, model: TetraModel, eps, w, stream) -> int:
+    return lib().tetra_eig(plan, ctypes.byref(model), eps, w, stream)
+
+
+def tetra_eig_backward(plan, model: TetraModel, grad_eps, grad_w, grad_params, ws, ws_bytes,
+                       stream) -> int:
+    return lib().tetra_eig_backward(plan, ctypes.byref(model), grad_eps, grad_w, grad_params, ws,
+                                    ws_bytes, stream)
+
+
+def tetra_eig_workspace_bytes(plan, n_R: int) -> int:
+    return int(lib().tetra_eig_workspace_bytes(plan, int(n_R)))
+
+
+def tetra_workspace_status(ws, stream) -> int:
+    return lib().tetra_workspace_status(ws, stream)
+
+
+def tetra_strerror(status: int) -> str:
+    return lib().tetra_strerror(int(status)).decode()
+
+
+def tetra_version() -> str:
+    return lib().tetra_version().decode()
+
+
+# ------------------------------------------------------------------ tensor convenience
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class Plan:
+    """A tetra plan plus tensor-level calls (PyTorch for memory and streams)."""
+
+    def __init__(self, n1, n2, n3, n_bands, n_orb, n_omega, mode="point", weight_dtype="f32",
+                 z_range=None, device=None):
+        torch = _torch()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        z0, z1 = (0, 0) if z_range is None else z_range
+        self.desc = TetraDesc(n1, n2, n3, n_bands, n_orb, n_omega, _MODES[mode],
+                              _DTYPES[weight_dtype], z0, z1)
+        self.mode = mode
+        self.weight_dtype = weight_dtype
+        self.device = dev
+        with torch.cuda.device(dev):
+            self.handle = tetra_plan(self.desc, dev)
+        self.layout = tetra_layout(self.handle)
+        self.workspace_bytes = tetra_workspace_bytes(self.handle)
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _LIB is not None:
+            _LIB.tetra_plan_destroy(h)
+            self.handle = None
+
+    # memory helpers -----------------------------------------------------
+    @property
+    def torch_weight_dtype(self):
+        torch = _torch()
+        return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.weight_dtype]
+
+    def empty_inputs(self):
+        """(eps, w) device tensors shaped (nz, ny, nx, stride) in the tetra layout."""
+        torch = _torch()
+        L = self.layout
+        dev = torch.device("cuda", self.device)
+        eps = torch.zeros((L.nz, L.ny, L.nx, L.eps_stride), dtype=torch.float32, device=dev)
+        w = torch.zeros((L.nz, L.ny, L.nx, L.w_stride), dtype=self.torch_weight_dtype, device=dev)
+        return eps, w
+
+    def workspace(self):
+        torch = _torch()
+        if self._ws is None:
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
+                                   device=torch.device("cuda", self.device))
+        return self._ws
+
+    # calls ----------------------------------------------------------------
+    def dos(self, eps, w, omega, out=None, stream=None):
+        torch = _torch()
+        no, nw = self.desc.n_orb, self.desc.n_omega
+        if out is None:
+            out = torch.empty((no, nw), dtype=torch.float32, device=eps.device)
+        ws = self.workspace()
+        _check(tetra_dos(self.handle, _ptr(eps), _ptr(w), _ptr(omega), _ptr(out), _ptr(ws),
+                         ws.numel(), _stream_handle(stream)), "tetra_dos")
+        return out
+
+    def dos_backward(self, eps, w, omega, grad_dos, grad_eps=None, grad_w=None, stream=None):
+        torch = _torch()
+        if grad_eps is None:
+            grad_eps = torch.empty(eps.shape, dtype=torch.float32, device=eps.device)
+        if grad_w is None:
+            grad_w = torch.empty(w.shape, dtype=torch.float32, device=w.device)
+        ws = self.workspace()
+        _check(tetra_dos_backward(self.handle, _ptr(eps), _ptr(w), _ptr(omega),
+                                  _ptr(grad_dos.contiguous()), _ptr(grad_eps), _ptr(grad_w),
+                                  _ptr(ws), ws.numel(), _stream_handle(stream)), "tetra_dos_backward")
+        return grad_eps, grad_w
+
+    def _model(self, params, R):
+        n_orb = self.desc.n_bands
+        return TetraModel(n_orb, int(R.shape[0]), _ptr(params), _ptr(R))
+
+    def eig(self, params, R, eps=None, w=None, stream=None):
+        """params: float32 device [n_orb + 2 n_R n_orb^2]; R: int32 device [n_R, 3]."""
+        if eps is None or w is None:
+            eps, w = self.empty_inputs()
+        m = self._model(params, R)
+        _check(tetra_eig(self.handle, m, _ptr(eps), _ptr(w), _stream_handle(stream)), "tetra_eig")
+        return eps, w
+
+    def eig_backward(self, params, R, grad_eps, grad_w, stream=None):
+        torch = _torch()
+        m = self._model(params, R)
+        nbytes = tetra_eig_workspace_bytes(self.handle, m.n_R)
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=params.device)
+        g = torch.empty_like(params)
+        _check(tetra_eig_backward(self.handle, m, _ptr(grad_eps), _ptr(grad_w), _ptr(g), _ptr(ws),
+                                  ws.numel(), _stream_handle(stream)), "tetra_eig_backward")
+        return g
+
+    def status(self, stream=None) -> int:
+        ws = self.workspace()
+        return tetra_workspace_status(_ptr(ws), _stream_handle(stream))

@@ -1,0 +1,743 @@
+// Forward kernel of the linear tetrahedron orbital-resolved DOS
+// (arXiv:1710.10789, Sec. II.C weights, Eqs. (8)-(9)) for sm_103a.
+//
+// Work decomposition
+//  * The cube grid [0,n1) x [0,n2) x [z0,z1) is cut into boxes of BX*BY*BZ
+//    cubes. A persistent CTA takes boxes blockIdx.x, blockIdx.x + gridDim.x, ...
+//    and, for each, has the box's (BX+1)(BY+1)(BZ+1) corner points of all
+//    bands (energies and orbital weights, tetra layout) copied into shared
+//    memory by two 4-D TMA loads, double buffered across boxes.
+//  * One thread handles one (tetrahedron, band) item: it reads the four corner
+//    energies, sorts them with a 5-comparator network carrying the corner
+//    positions (Sec. II.C sorts E1 <= E2 <= E3 <= E4), reads the orbital
+//    weights in sorted order, and visits only the energies strictly inside
+//    (E1, E4) (bins overlapping it in bin mode); all others get zero weight.
+//  * Each visited energy adds sum_l b_{l,s} dw_l to the CTA's tile for every
+//    orbital s (Eq. (8)).
+//
+// Accumulation: exact fixed point, no float atomics anywhere
+//  * Contributions are scaled by 1/u, u = (V_T/V_G) / dE * 2^-F (dE = mean
+//    grid spacing, F = fixed_bits), rounded to integers and added with integer
+//    shared-memory atomics into an int32 tile [n_orb][energies]. Integer
+//    addition is associative, so the tile does not depend on thread order.
+//  * A per-item bound q_max (|b| <= Bmax of the box, and the tetrahedron DOS
+//    is at most 3/E41 of V_T/V_G) decides between this fast path and a 64-bit
+//    global integer path for rare near-flat tetrahedra. The sum of q_max over
+//    processed items bounds every tile entry; the tile is flushed into the
+//    CTA's int64 partial in global memory before it could overflow.
+//  * tetra_dos_reduce sums the per-CTA int64 partials (exact) and scales by u.
+#include "tetra_internal.cuh"
+
+namespace tetra {
+
+namespace {
+
+constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float + kMagic rounds to an integer
+constexpr int kMagicBits = 0x4B400000;  // bit pattern of kMagic
+constexpr int kThreads = 512;
+constexpr uint32_t kSmemAlign = 1024;
+constexpr unsigned kFlushAt = 1u << 30;
+constexpr int kBuckets = 64;   // window-length classes for grouping items
+
+// Table I, corner labels minus one; label c sits at offset (c&1, (c>>1)&1, (c>>2)&1).
+__constant__ int c_table[6][4] = {{0, 1, 2, 5}, {1, 2, 3, 5}, {0, 2, 4, 5},
+                                  {2, 3, 5, 7}, {2, 4, 5, 6}, {2, 5, 6, 7}};
+
+struct FwdArgs {
+    int n1, n2, n3, nb, n_orb, n_omega;
+    int z0, z1;
+    int BX, BY, BZ, nbx, nby, n_boxes;
+    int eps_stride, w_stride;
+    uint32_t e_box_bytes, w_box_bytes, w_box_off, stage_bytes;   // w box at stage + w_box_off (128-aligned)
+    int chunk_w;
+    int items_per_box;
+    int fast_cap;
+    int fixed_bits;
+    double vtvg;
+    const float *omega;
+    long long *G;   // [n_chunks][grid_x][n_orb][chunk_w]
+    int *status;
+};
+
+// Fixed-point unit, identical in every kernel that uses it.
+__device__ __forceinline__ double fixed_unit(const float *omega, int n_omega, int mode, double vtvg,
+                                             int bits) {
+    double de;
+    if (mode == TETRA_POINT)
+        de = n_omega > 1 ? ((double)omega[n_omega - 1] - (double)omega[0]) / (n_omega - 1) : 1.0;
+    else
+        de = ((double)omega[n_omega] - (double)omega[0]) / n_omega;
+    if (!(de > 0.0)) de = 1.0;
+    return vtvg / de * ldexp(1.0, -bits);
+}
+
+__device__ __forceinline__ void cswap(float &ea, float &eb, int &pa, int &pb) {
+    const bool s = eb < ea;
+    const float lo = s ? eb : ea, hi = s ? ea : eb;
+    const int plo = s ? pb : pa, phi = s ? pa : pb;
+    ea = lo; eb = hi; pa = plo; pb = phi;
+}
+
+// Dither offset in [-1/2, 1/2) for one (tetrahedron, band) item, hashed from its
+// global identity so it does not depend on the launch shape.
+__device__ __forceinline__ float item_dither(uint32_t key) {
+    uint32_t h = key * 0x9E3779B9u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
+}
+
+__device__ __forceinline__ float safe_rcp(float x) { return x > 0.f ? __fdividef(1.0f, x) : 0.f; }
+
+// Per-item constants of the weight formulas, in fixed-point units.
+struct Tet {
+    float e1, e2, e3, e4;
+    float r21, r31, r41, r32, r42, r43;
+    float P1, S1, P3, S3, k1, k2, k3, fq;
+};
+
+__device__ __forceinline__ void tet_setup(Tet &T, float e1, float e2, float e3, float e4, float fq) {
+    T.e1 = e1; T.e2 = e2; T.e3 = e3; T.e4 = e4;
+    T.r21 = safe_rcp(e2 - e1); T.r31 = safe_rcp(e3 - e1); T.r41 = safe_rcp(e4 - e1);
+    T.r32 = safe_rcp(e3 - e2); T.r42 = safe_rcp(e4 - e2); T.r43 = safe_rcp(e4 - e3);
+    T.P1 = 4.f * fq * T.r21 * T.r31 * T.r41;
+    T.S1 = T.r21 + T.r31 + T.r41;
+    T.P3 = 4.f * fq * T.r41 * T.r42 * T.r43;
+    T.S3 = T.r41 + T.r42 + T.r43;
+    T.k1 = fq * T.r31 * T.r41;
+    T.k2 = fq * T.r31 * T.r32 * T.r41;
+    T.k3 = fq * T.r32 * T.r41 * T.r42;
+    T.fq = fq;
+}
+
+// Point-mode constants of one item, for a branch-free evaluation of the four
+// corner derivatives dw_l/dE at any E strictly inside (E1, E4):
+//  * cases E1 < E <= E2 and E3 < E < E4 share one mirrored form: with
+//    v = E - E1 (or E4 - E), g = P v^2, the apex corner (1, or 4) gets
+//    g (3 - v S) and the other three g v / E_j1 (or g v / E_4j);
+//  * in E2 < E <= E3 every dw_l is a cubic in t = E - E2, evaluated by
+//    Horner from coefficients expanded from the printed C1, C2, C3 forms.
+struct TetP {
+    float e1, e2, e3, e4;
+    float P1, S1, r21, r31, r41;
+    float P3, S3, r42, r43;
+    float c[4][4];   // c[l][m]: coefficient of t^m in dw_l (case E2 < E <= E3)
+};
+
+__device__ __forceinline__ void tetp_setup(TetP &T, float e1, float e2, float e3, float e4, float fq) {
+    T.e1 = e1; T.e2 = e2; T.e3 = e3; T.e4 = e4;
+    const float A = e2 - e1, B = e3 - e2, C = e4 - e2;
+    T.r21 = safe_rcp(A); T.r31 = safe_rcp(e3 - e1); T.r41 = safe_rcp(e4 - e1);
+    const float r32 = safe_rcp(B);
+    T.r42 = safe_rcp(C); T.r43 = safe_rcp(e4 - e3);
+    T.P1 = 4.f * fq * T.r21 * T.r31 * T.r41;
+    T.S1 = T.r21 + T.r31 + T.r41;
+    T.P3 = 4.f * fq * T.r41 * T.r42 * T.r43;
+    T.S3 = T.r41 + T.r42 + T.r43;
+    const float r31 = T.r31, r41 = T.r41, r42 = T.r42;
+    const float k1 = fq * r31 * r41, k2 = fq * r31 * r32 * r41, k3 = fq * r32 * r41 * r42;
+    const float k1r31 = k1 * r31, k1r41 = k1 * r41, k2r31 = k2 * r31, k2r41 = k2 * r41;
+    const float k2r32 = k2 * r32, k3r41 = k3 * r41, k3r32 = k3 * r32, k3r42 = k3 * r42;
+    T.c[0][0] = -A * (A * (k1r31 + k1r41) - B * B * k2r31 - B * C * k2r41 - 2.f * B * k1r31 -
+                      2.f * C * k1r41 - 2.f * k1);
+    T.c[0][1] = -2.f * (2.f * A * B * k2r31 + A * B * k2r41 + A * C * k2r41 + 2.f * A * k1r31 +
+                        2.f * A * k1r41 - B * B * k2r31 - B * C * k2r41 - B * k1r31 -
+                        C * C * k3r41 - C * k1r41 - k1);
+    T.c[0][2] = -3.f * (-A * k2r31 - A * k2r41 + 2.f * B * k2r31 + B * k2r41 + C * k2r41 +
+                        2.f * C * k3r41 + k1r31 + k1r41);
+    T.c[0][3] = 4.f * (k2r31 + k2r41 + k3r41);
+    T.c[1][0] = A * (B * B * k2r32 + B * k2 + 2.f * k1);
+    T.c[1][1] = -2.f * (2.f * A * B * k2r32 + A * k2 - B * B * k2r32 - B * C * k3r32 - B * k2 -
+                        C * C * k3r42 - C * k3 - k1);
+    T.c[1][2] = 3.f * (A * k2r32 - 2.f * B * k2r32 - B * k3r32 - C * k3r32 - 2.f * C * k3r42 - k2 - k3);
+    T.c[1][3] = 4.f * (k2r32 + k3r32 + k3r42);
+    T.c[2][0] = A * A * r31 * (B * k2 + 3.f * k1);
+    T.c[2][1] = 2.f * A * (-A * k2r31 + 2.f * B * k2r31 + B * k2r32 + 3.f * k1r31);
+    T.c[2][2] = 3.f * (-2.f * A * k2r31 - A * k2r32 + B * k2r31 + B * k2r32 + C * k3r32 + k1r31);
+    T.c[2][3] = -4.f * (k2r31 + k2r32 + k3r32);
+    T.c[3][0] = A * A * r41 * (B * k2 + 3.f * k1);
+    T.c[3][1] = 2.f * A * r41 * (-A * k2 + 2.f * B * k2 + C * k3 + 3.f * k1);
+    T.c[3][2] = 3.f * (-2.f * A * k2r41 - A * k3r41 + B * k2r41 + C * k3r41 + C * k3r42 + k1r41);
+    T.c[3][3] = -4.f * (k2r41 + k3r41 + k3r42);
+}
+
+__device__ __forceinline__ void tetp_dw(const TetP &T, float E, float d[4]) {
+    const bool in1 = E <= T.e2;
+    const bool in3 = E > T.e3;
+    const float v = in1 ? E - T.e1 : T.e4 - E;
+    const float P = in1 ? T.P1 : T.P3;
+    const float S = in1 ? T.S1 : T.S3;
+    const float ra = in1 ? T.r21 : T.r41, rb = in1 ? T.r31 : T.r42, rc = in1 ? T.r41 : T.r43;
+    const float g = P * v * v;
+    const float apex = g * fmaf(-v, S, 3.f);
+    const float u = g * v;
+    const float o1 = u * ra, o2 = u * rb, o3 = u * rc;
+    const float t = E - T.e2;
+    float h[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) h[l] = fmaf(fmaf(fmaf(T.c[l][3], t, T.c[l][2]), t, T.c[l][1]), t, T.c[l][0]);
+    const bool in2 = !in1 && !in3;
+    d[0] = in2 ? h[0] : (in1 ? apex : o1);
+    d[1] = in2 ? h[1] : (in1 ? o1 : o2);
+    d[2] = in2 ? h[2] : (in1 ? o2 : o3);
+    d[3] = in2 ? h[3] : (in1 ? o3 : apex);
+}
+
+// w_l(E) for any E (Sec. II.C, all five cases), sorted corners.
+__device__ __forceinline__ void tet_weights(const Tet &T, float E, float w[4]) {
+    if (E <= T.e1) {
+        w[0] = w[1] = w[2] = w[3] = 0.f;
+    } else if (E >= T.e4) {
+        w[0] = w[1] = w[2] = w[3] = T.fq;
+    } else if (E <= T.e2) {
+        const float x = E - T.e1;
+        const float C = 0.25f * T.P1 * x * x * x;
+        w[0] = C * fmaf(-x, T.S1, 4.f);
+        const float cx = C * x;
+        w[1] = cx * T.r21; w[2] = cx * T.r31; w[3] = cx * T.r41;
+    } else if (E <= T.e3) {
+        const float a = E - T.e1, bq = E - T.e2, c = T.e3 - E, dd = T.e4 - E;
+        const float C1 = T.k1 * a * a;
+        const float C2 = T.k2 * a * bq * c;
+        const float C3 = T.k3 * bq * bq * dd;
+        const float S12 = C1 + C2, S23 = C2 + C3, S123 = S12 + C3;
+        w[0] = C1 + S12 * c * T.r31 + S123 * dd * T.r41;
+        w[1] = S123 + S23 * c * T.r32 + C3 * dd * T.r42;
+        w[2] = S12 * a * T.r31 + S23 * bq * T.r32;
+        w[3] = S123 * a * T.r41 + C3 * bq * T.r42;
+    } else {
+        const float y = T.e4 - E;
+        const float C = 0.25f * T.P3 * y * y * y;
+        const float cy = C * y;
+        w[0] = T.fq - cy * T.r41; w[1] = T.fq - cy * T.r42; w[2] = T.fq - cy * T.r43;
+        w[3] = T.fq - C * fmaf(-y, T.S3, 4.f);
+    }
+}
+
+// Adds one energy's contribution of an item directly to the CTA's int64
+// partial (global integer atomics): the path of the rare items whose bound
+// does not fit the int32 tile. Same dithered single rounding as the tile path:
+// round(c + delta - 1/2) with delta in [0,1) hashed from the item.
+template <int NORB>
+__device__ __forceinline__ void deposit_slow(const float (&b)[4][NORB], const float d[4], int n_orb,
+                                             float dith, long long *gcol, int g_stride, int *status) {
+#pragma unroll
+    for (int s = 0; s < NORB; ++s) {
+        if (s < n_orb) {
+            float acc = fmaf(b[0][s], d[0], dith);
+            acc = fmaf(b[1][s], d[1], acc);
+            acc = fmaf(b[2][s], d[2], acc);
+            acc = fmaf(b[3][s], d[3], acc);
+            if (fabsf(acc) < 9.0e18f) {
+                const long long q = __float2ll_rn(acc);
+                if (q != 0)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(gcol + (long)s * g_stride),
+                              static_cast<unsigned long long>(q));
+            } else {
+                atomicOr(status, kFlagRange);
+            }
+        }
+    }
+}
+
+// Energy window of one item, as global indices clipped to this CTA's chunk
+// [w0, w0+wc): point mode, energies strictly inside (e1, e4); bin mode, bins
+// whose weight difference can be non-zero (upper edge > e1, and lower edge
+// < e4 or <= e1). The estimate from the mean spacing is corrected against the
+// cached grid, so any ascending grid gives the exact window.
+template <int MODE>
+__device__ __forceinline__ void item_window(float e1, float e4, const float *om, int w0, int wc,
+                                            float om0, float inv_de, int n_omega, int &lo, int &hi) {
+    const float flo = fminf(fmaxf((e1 - om0) * inv_de, -2.f), (float)n_omega + 2.f);
+    const float fhi = fminf(fmaxf((e4 - om0) * inv_de, -2.f), (float)n_omega + 2.f);
+    if (MODE == TETRA_POINT) {
+        lo = min(max((int)floorf(flo) + 1, w0), w0 + wc);
+        hi = max(min((int)ceilf(fhi) - 1, w0 + wc - 1), w0 - 1);
+        while (lo > w0 && om[lo - 1 - w0] > e1) --lo;
+        while (lo < w0 + wc && om[lo - w0] <= e1) ++lo;
+        while (hi < w0 + wc - 1 && om[hi + 1 - w0] < e4) ++hi;
+        while (hi >= w0 && om[hi - w0] >= e4) --hi;
+    } else {
+        lo = min(max((int)floorf(flo), w0), w0 + wc);
+        hi = max(min((int)ceilf(fhi), w0 + wc - 1), w0 - 1);
+        while (lo > w0 && om[lo - w0] > e1) --lo;
+        while (lo < w0 + wc && om[lo + 1 - w0] <= e1) ++lo;
+        while (hi < w0 + wc - 1 && (om[hi + 1 - w0] < e4 || om[hi + 1 - w0] <= e1)) ++hi;
+        while (hi >= w0 && !(om[hi - w0] < e4 || om[hi - w0] <= e1)) --hi;
+    }
+}
+
+// Orbital weights of one corner of band n, as floats.
+template <int NORB, typename WT>
+__device__ __forceinline__ void load_weights(const WT *src, int n_orb, float (&b)[NORB]) {
+    constexpr int VEC = 16 / sizeof(WT);
+    if (NORB % VEC == 0 && n_orb == NORB) {
+#pragma unroll
+        for (int v = 0; v < NORB / VEC; ++v) {
+            const uint4 q = reinterpret_cast<const uint4 *>(src)[v];
+            const WT *e = reinterpret_cast<const WT *>(&q);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) b[v * VEC + j] = to_f32<WT>(e[j]);
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < NORB; ++s) b[s] = (s < n_orb) ? to_f32<WT>(src[s]) : 0.f;
+    }
+}
+
+template <int NORB, typename WT, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    tetra_dos_fwd_kernel(const __grid_constant__ CUtensorMap tm_eps,
+                         const __grid_constant__ CUtensorMap tm_w, const FwdArgs A) {
+    constexpr int TS = NORB + 1;   // tile row: NORB orbitals + 1 pad (spreads banks)
+    extern __shared__ unsigned char smem_raw[];
+    // TMA destinations need an aligned base; the dynamic area starts after the
+    // static variables, so align it here (the host reserves kSmemAlign bytes).
+    unsigned char *smem = smem_raw + ((kSmemAlign - (smem_u32(smem_raw) & (kSmemAlign - 1))) &
+                                      (kSmemAlign - 1));
+    const int tid = threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int w0 = chunk * A.chunk_w;
+    const int wc = min(A.chunk_w, A.n_omega - w0);
+    // shared memory carve-up
+    unsigned char *stage[2] = {smem, smem + A.stage_bytes};
+    int *tile = reinterpret_cast<int *>(smem + 2 * A.stage_bytes);   // [chunk_w][TS]
+    float *om = reinterpret_cast<float *>(tile + TS * A.chunk_w);   // energies / edges
+    float *iw = om + A.chunk_w + 1;                                   // 1/bin width (bin mode)
+    unsigned *blk_bound = reinterpret_cast<unsigned *>(iw + (MODE == TETRA_BIN ? A.chunk_w : 0));
+    const int n_blk = (A.chunk_w + 63) >> 6;
+    short *s_lo = reinterpret_cast<short *>(blk_bound + n_blk);      // window start - w0
+    unsigned short *s_K = reinterpret_cast<unsigned short *>(s_lo + A.items_per_box);
+    unsigned short *s_list = s_K + A.items_per_box;                 // items sorted by K
+    int *hist = reinterpret_cast<int *>(
+        (reinterpret_cast<uintptr_t>(s_list + A.items_per_box) + 15) & ~uintptr_t(15));
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(hist + 2 * kBuckets);
+    __shared__ float red_f[kThreads / 32];
+    __shared__ int s_abort, s_active;
+
+    // self-check of the shared-memory carve-up against the launch's dynamic size
+    {
+        const uintptr_t need = reinterpret_cast<uintptr_t>(mbar + 2) - reinterpret_cast<uintptr_t>(smem_raw);
+        const bool bad = need > dynamic_smem_bytes() || (smem_u32(stage[0]) & 127u) != 0 ||
+                         (smem_u32(stage[1]) & 127u) != 0 || (A.w_box_off & 127u) != 0 ||
+                         A.w_box_off < A.e_box_bytes || A.w_box_off + A.w_box_bytes > A.stage_bytes ||
+                         (smem_u32(mbar) & 7u) != 0 || A.items_per_box > 65535;
+        if (bad) {
+            if (tid == 0) atomicOr(A.status, kFlagConfig);
+            return;
+        }
+    }
+    for (int i = tid; i < TS * A.chunk_w; i += blockDim.x) tile[i] = 0;
+    for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
+    const int n_om = (MODE == TETRA_POINT) ? wc : wc + 1;
+    for (int i = tid; i < n_om; i += blockDim.x) om[i] = A.omega[w0 + i];
+    if (tid == 0) {
+        s_abort = 0;
+        prefetch_tensormap(&tm_eps);
+        prefetch_tensormap(&tm_w);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (MODE == TETRA_BIN)
+        for (int i = tid; i < wc; i += blockDim.x) iw[i] = 1.0f / (om[i + 1] - om[i]);
+
+    // grid-wide energy constants
+    const double u = fixed_unit(A.omega, A.n_omega, MODE, A.vtvg, A.fixed_bits);
+    const float fq = (float)(0.25 * A.vtvg / u);   // V_T/(4 V_G) in fixed-point units
+    const float om0 = A.omega[0];
+    const float omN = (MODE == TETRA_POINT) ? A.omega[A.n_omega - 1] : A.omega[A.n_omega];
+    const float inv_de =
+        (MODE == TETRA_POINT) ? (A.n_omega > 1 ? (float)(A.n_omega - 1) / (omN - om0) : 0.f)
+                              : (float)A.n_omega / (omN - om0);
+    float max_iw = 0.f;
+    if (MODE == TETRA_BIN) {
+        // every CTA needs the narrowest bin of the whole grid for the bound
+        for (int i = tid; i < A.n_omega; i += blockDim.x)
+            max_iw = fmaxf(max_iw, 1.0f / (A.omega[i + 1] - A.omega[i]));
+        for (int o = 16; o; o >>= 1) max_iw = fmaxf(max_iw, __shfl_xor_sync(0xffffffffu, max_iw, o));
+        if ((tid & 31) == 0) red_f[tid >> 5] = max_iw;
+        __syncthreads();
+        max_iw = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) max_iw = fmaxf(max_iw, red_f[i]);
+        __syncthreads();
+    }
+
+    const int PX = A.BX + 1, PY = A.BY + 1;
+    const int ncube = A.BX * A.BY * A.BZ;
+    long long *Gc = A.G + ((long)chunk * gridDim.x + blockIdx.x) * (long)A.n_orb * A.chunk_w;
+
+    // prologue: first two boxes
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            const int box = blockIdx.x + k * gridDim.x;
+            if (box >= A.n_boxes) break;
+            const int ix = box % A.nbx, iy = (box / A.nbx) % A.nby, iz = box / (A.nbx * A.nby);
+            mbar_arrive_expect_tx(&mbar[k], A.e_box_bytes + A.w_box_bytes);
+            tma_load_4d(stage[k], &tm_eps, 0, ix * A.BX, iy * A.BY, A.z0 + iz * A.BZ, &mbar[k]);
+            tma_load_4d(stage[k] + A.w_box_off, &tm_w, 0, ix * A.BX, iy * A.BY,
+                        A.z0 + iz * A.BZ, &mbar[k]);
+        }
+    }
+
+    for (int k = 0;; ++k) {
+        const int box = blockIdx.x + k * gridDim.x;
+        if (box >= A.n_boxes) break;
+        const int st = k & 1;
+        if (tid < kBuckets) hist[tid] = 0;
+        const bool ok = mbar_wait_bounded(&mbar[st], (k >> 1) & 1, A.status);
+        if (__syncthreads_or(!ok)) {
+            s_abort = 1;
+            break;
+        }
+        const float *Es = reinterpret_cast<const float *>(stage[st]);
+        const WT *Ws = reinterpret_cast<const WT *>(stage[st] + A.w_box_off);
+        const int ix = box % A.nbx, iy = (box / A.nbx) % A.nby, iz = box / (A.nbx * A.nby);
+        const int gx0 = ix * A.BX, gy0 = iy * A.BY, gz0 = A.z0 + iz * A.BZ;
+
+        // Bmax = max |w| over the staged box (all of it, padding included, so it
+        // bounds every orbital weight an item can read)
+        float bmax = 0.f;
+        {
+            const int n16 = (int)(A.w_box_bytes >> 4);
+            const uint4 *src = reinterpret_cast<const uint4 *>(stage[st] + A.w_box_off);
+            for (int i = tid; i < n16; i += blockDim.x) {
+                const uint4 v = src[i];
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (sizeof(WT) == 4) {
+                        bmax = fmaxf(bmax, fabsf(__uint_as_float(wv[q])));
+                    } else {
+                        const WT lo = *reinterpret_cast<const WT *>(&wv[q]);
+                        const WT hi = *(reinterpret_cast<const WT *>(&wv[q]) + 1);
+                        bmax = fmaxf(bmax, fmaxf(fabsf(to_f32<WT>(lo)), fabsf(to_f32<WT>(hi))));
+                    }
+                }
+            }
+        }
+
+        // Pass A: window of every item (corner min / max only), histogram of its
+        // length K, so that pass B can hand items of similar length to the same
+        // warp. The integers an item adds do not depend on which thread adds
+        // them, so the grouping cannot change the result.
+        for (int it = tid; it < A.items_per_box; it += blockDim.x) {
+            const int cube = it % ncube;
+            const int t = (it / ncube) % 6;
+            const int n = it / (6 * ncube);
+            const int cx = cube % A.BX, cy = (cube / A.BX) % A.BY, cz = cube / (A.BX * A.BY);
+            int K = 0, lo = 0;
+            if (gx0 + cx < A.n1 && gy0 + cy < A.n2 && gz0 + cz < A.z1) {
+                float e1 = 3.0e38f, e4 = -3.0e38f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = c_table[t][q];
+                    const int p = (cx + (c & 1)) + PX * ((cy + ((c >> 1) & 1)) + PY * (cz + ((c >> 2) & 1)));
+                    const float ev = Es[p * A.eps_stride + n];
+                    e1 = fminf(e1, ev);
+                    e4 = fmaxf(e4, ev);
+                }
+                int hi;
+                item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, A.n_omega, lo, hi);
+                K = max(0, hi - lo + 1);
+            }
+            s_lo[it] = (short)(lo - w0);
+            s_K[it] = (unsigned short)K;
+            if (K > 0) atomicAdd(&hist[min(K, kBuckets - 1)], 1);
+        }
+        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        if ((tid & 31) == 0) red_f[tid >> 5] = bmax;
+        __syncthreads();
+        // exclusive scan of the histogram into cursors (one warp)
+        if (tid < 32) {
+            int carry = 0;
+            for (int b0 = 0; b0 < kBuckets; b0 += 32) {
+                const int v = hist[b0 + tid];
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (tid >= o) x += y;
+                }
+                hist[kBuckets + b0 + tid] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (tid == 0) s_active = carry;
+        }
+        bmax = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) bmax = fmaxf(bmax, red_f[i]);
+        __syncthreads();
+        for (int it = tid; it < A.items_per_box; it += blockDim.x) {
+            const int K = s_K[it];
+            if (K > 0) s_list[atomicAdd(&hist[kBuckets + min(K, kBuckets - 1)], 1)] = (unsigned short)it;
+        }
+        __syncthreads();
+        const int n_active = s_active;
+
+        // Pass B: items in order of window length
+        for (int r = tid; r < n_active; r += blockDim.x) {
+            const int it = s_list[r];
+            const int cube = it % ncube;
+            const int t = (it / ncube) % 6;
+            const int n = it / (6 * ncube);
+            const int cx = cube % A.BX, cy = (cube / A.BX) % A.BY, cz = cube / (A.BX * A.BY);
+            float e[4];
+            int p[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c_table[t][q];
+                p[q] = (cx + (c & 1)) + PX * ((cy + ((c >> 1) & 1)) + PY * (cz + ((c >> 2) & 1)));
+                e[q] = Es[p[q] * A.eps_stride + n];
+            }
+            cswap(e[0], e[1], p[0], p[1]);
+            cswap(e[2], e[3], p[2], p[3]);
+            cswap(e[0], e[2], p[0], p[2]);
+            cswap(e[1], e[3], p[1], p[3]);
+            cswap(e[1], e[2], p[1], p[2]);
+            const int lo = w0 + s_lo[it];
+            const int hi = lo + s_K[it] - 1;
+            float b[4][NORB];
+#pragma unroll
+            for (int r4 = 0; r4 < 4; ++r4)
+                load_weights<NORB, WT>(Ws + (long)p[r4] * A.w_stride + n * A.n_orb, A.n_orb, b[r4]);
+            // per-item bound on every |contribution|, in fixed-point units
+            float qmax;
+            if (MODE == TETRA_POINT)
+                qmax = bmax * 4.f * fq * 3.1f * safe_rcp(e[3] - e[0]);
+            else
+                qmax = bmax * 4.f * fq * max_iw * 1.01f;
+            if (!(e[3] > e[0])) qmax = 3.0e38f;
+            const bool fast = qmax < (float)A.fast_cap;
+            const uint32_t gcube = (uint32_t)(gx0 + cx) +
+                                   (uint32_t)A.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)A.n2 * (uint32_t)(gz0 + cz));
+            const float dith = item_dither((gcube * 6u + (uint32_t)t) * (uint32_t)A.nb + (uint32_t)n);
+            if (fast) {
+                // every tile entry of these blocks may receive at most qmax from this item
+                const unsigned qb = (unsigned)qmax + 2u;
+                for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qb);
+            }
+            if (MODE == TETRA_POINT) {
+                TetP TP;
+                tetp_setup(TP, e[0], e[1], e[2], e[3], fq);
+                if (fast) {
+                    int *col = tile + (lo - w0) * TS;
+                    for (int i = lo; i <= hi; ++i, col += TS) {
+                        float d[4];
+                        tetp_dw(TP, om[i - w0], d);
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            float acc = fmaf(b[0][s], d[0], dith);
+                            acc = fmaf(b[1][s], d[1], acc);
+                            acc = fmaf(b[2][s], d[2], acc);
+                            acc = fmaf(b[3][s], d[3], acc);
+                            atomicAdd(col + s, __float_as_int(acc + kMagic) - kMagicBits);
+                        }
+                    }
+                } else {
+                    for (int i = lo; i <= hi; ++i) {
+                        float d[4];
+                        tetp_dw(TP, om[i - w0], d);
+                        deposit_slow<NORB>(b, d, A.n_orb, dith, Gc + (i - w0), A.chunk_w, A.status);
+                    }
+                }
+            } else {
+                Tet T;
+                tet_setup(T, e[0], e[1], e[2], e[3], fq);
+                float wp[4];
+                tet_weights(T, om[lo - w0], wp);
+                int *col = tile + (lo - w0) * TS;
+                for (int i = lo; i <= hi; ++i, col += TS) {
+                    float wn[4], d[4];
+                    tet_weights(T, om[i + 1 - w0], wn);
+                    const float sc = iw[i - w0];
+#pragma unroll
+                    for (int r4 = 0; r4 < 4; ++r4) { d[r4] = (wn[r4] - wp[r4]) * sc; wp[r4] = wn[r4]; }
+                    if (fast) {
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            float acc = fmaf(b[0][s], d[0], dith);
+                            acc = fmaf(b[1][s], d[1], acc);
+                            acc = fmaf(b[2][s], d[2], acc);
+                            acc = fmaf(b[3][s], d[3], acc);
+                            atomicAdd(col + s, __float_as_int(acc + kMagic) - kMagicBits);
+                        }
+                    } else {
+                        deposit_slow<NORB>(b, d, A.n_orb, dith, Gc + (i - w0), A.chunk_w, A.status);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // every thread is done reading stage[st] and adding to the tile
+        // refill this stage with box k+2
+        if (tid == 0) {
+            const int nbox = box + 2 * gridDim.x;
+            if (nbox < A.n_boxes) {
+                fence_proxy_async_smem();
+                const int jx = nbox % A.nbx, jy = (nbox / A.nbx) % A.nby, jz = nbox / (A.nbx * A.nby);
+                mbar_arrive_expect_tx(&mbar[st], A.e_box_bytes + A.w_box_bytes);
+                tma_load_4d(stage[st], &tm_eps, 0, jx * A.BX, jy * A.BY, A.z0 + jz * A.BZ, &mbar[st]);
+                tma_load_4d(stage[st] + A.w_box_off, &tm_w, 0, jx * A.BX, jy * A.BY,
+                            A.z0 + jz * A.BZ, &mbar[st]);
+            }
+        }
+        // A block whose bound reached kFlushAt is moved into the CTA's int64
+        // partial before the next box: one box adds less than 2^30 - 2^20 to any
+        // entry (per-item cap x items per box), so entries stay below 2^31.
+        const bool mine = tid < n_blk && blk_bound[tid] >= kFlushAt;
+        if (__syncthreads_or(mine)) {
+            for (int bk = 0; bk < n_blk; ++bk) {
+                if (blk_bound[bk] < kFlushAt) continue;   // uniform: every thread reads the same value
+                const int j0 = bk << 6, jn = min(64, wc - j0);
+                for (int i = tid; i < A.n_orb * 64; i += blockDim.x) {
+                    const int s = i >> 6, j = i & 63;
+                    if (j >= jn) continue;
+                    int *e = tile + (j0 + j) * TS + s;
+                    const int v = *e;
+                    if (v) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j0 + j),
+                                  static_cast<unsigned long long>(static_cast<long long>(v)));
+                        *e = 0;
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid < n_blk && blk_bound[tid] >= kFlushAt) blk_bound[tid] = 0;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        // a TMA wait timed out: wait (bounded) for copies still in flight, then leave
+        if (tid == 0) {
+            for (int k = 0; k < 2; ++k) mbar_wait_bounded(&mbar[k], 0, nullptr, 100000000ull);
+        }
+        return;
+    }
+    for (int i = tid; i < A.n_orb * wc; i += blockDim.x) {
+        const int s = i / wc, j = i - s * wc;
+        const int v = tile[j * TS + s];
+        if (v)
+            atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j),
+                      static_cast<unsigned long long>(static_cast<long long>(v)));
+    }
+}
+
+// dos[s][w0+j] = u * sum over CTAs of the int64 partials (exact integer sum).
+__global__ void tetra_dos_reduce_kernel(const long long *G, int grid_x, int n_orb, int n_omega,
+                                        int chunk_w, int mode, const float *omega, double vtvg,
+                                        int bits, float *dos) {
+    const double u = fixed_unit(omega, n_omega, mode, vtvg, bits);
+    const long total = (long)n_orb * n_omega;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / n_omega), i = (int)(idx - (long)s * n_omega);
+        const int chunk = i / chunk_w, j = i - chunk * chunk_w;
+        const long long *g = G + ((long)chunk * grid_x * n_orb + s) * chunk_w + j;
+        long long acc = 0;
+        for (int c = 0; c < grid_x; ++c) acc += g[(long)c * n_orb * chunk_w];
+        dos[idx] = (float)((double)acc * u);
+    }
+}
+
+template <int NORB, typename WT, int MODE>
+cudaError_t launch_t(const Plan &P, const CUtensorMap &te, const CUtensorMap &tw, const FwdArgs &A,
+                     cudaStream_t stream) {
+    auto k = tetra_dos_fwd_kernel<NORB, WT, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P.smem_bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid(P.grid_x, P.n_chunks);
+    k<<<grid, kThreads, P.smem_bytes, stream>>>(te, tw, A);
+    return cudaGetLastError();
+}
+
+template <int NORB, int MODE>
+cudaError_t launch_wt(const Plan &P, const CUtensorMap &te, const CUtensorMap &tw,
+                      const FwdArgs &A, cudaStream_t stream) {
+    switch (P.d.weight_dtype) {
+        case TETRA_F16: return launch_t<NORB, __half, MODE>(P, te, tw, A, stream);
+        case TETRA_BF16: return launch_t<NORB, __nv_bfloat16, MODE>(P, te, tw, A, stream);
+        default: return launch_t<NORB, float, MODE>(P, te, tw, A, stream);
+    }
+}
+
+template <int MODE>
+cudaError_t launch_norb(const Plan &P, const CUtensorMap &te, const CUtensorMap &tw,
+                        const FwdArgs &A, cudaStream_t stream) {
+    const int no = P.d.n_orb;
+    if (no <= 1) return launch_wt<1, MODE>(P, te, tw, A, stream);
+    if (no <= 2) return launch_wt<2, MODE>(P, te, tw, A, stream);
+    if (no <= 4) return launch_wt<4, MODE>(P, te, tw, A, stream);
+    if (no <= 8) return launch_wt<8, MODE>(P, te, tw, A, stream);
+    return launch_wt<16, MODE>(P, te, tw, A, stream);
+}
+
+}  // namespace
+
+int norb_template(int n_orb) {
+    return n_orb <= 1 ? 1 : n_orb <= 2 ? 2 : n_orb <= 4 ? 4 : n_orb <= 8 ? 8 : 16;
+}
+
+size_t dos_forward_workspace(const Plan &P) {
+    return kStatusBytes +
+           sizeof(long long) * (size_t)P.n_chunks * P.grid_x * P.d.n_orb * (size_t)P.chunk_w;
+}
+
+tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w,
+                                  const float *omega, float *dos, void *ws, size_t ws_bytes,
+                                  cudaStream_t stream) {
+    const size_t need = dos_forward_workspace(P);
+    if (ws_bytes < need) return TETRA_ENOMEM;
+    CUtensorMap te, tw;
+    const CUtensorMapDataType wdt = P.d.weight_dtype == TETRA_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                    : P.d.weight_dtype == TETRA_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    tetra_status_t st = encode_point_map(&te, eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.eps_stride,
+                                         P.nx, P.ny, P.nz, P.BX + 1, P.BY + 1, P.BZ + 1);
+    if (st != TETRA_OK) return st;
+    st = encode_point_map(&tw, w, wdt, P.wbytes, P.w_stride, P.nx, P.ny, P.nz, P.BX + 1, P.BY + 1,
+                          P.BZ + 1);
+    if (st != TETRA_OK) return st;
+    FwdArgs A;
+    A.n1 = P.d.n1; A.n2 = P.d.n2; A.n3 = P.d.n3; A.nb = P.d.n_bands; A.n_orb = P.d.n_orb;
+    A.n_omega = P.d.n_omega;
+    A.z0 = P.z0; A.z1 = P.z1;
+    A.BX = P.BX; A.BY = P.BY; A.BZ = P.BZ; A.nbx = P.nbx; A.nby = P.nby; A.n_boxes = P.n_boxes;
+    A.eps_stride = P.eps_stride; A.w_stride = P.w_stride;
+    const uint32_t npts = (uint32_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
+    A.e_box_bytes = npts * P.eps_stride * 4u;
+    A.w_box_bytes = npts * P.w_stride * (uint32_t)P.wbytes;
+    // every TMA destination starts on a 128-byte boundary
+    A.w_box_off = (A.e_box_bytes + 127u) & ~127u;
+    A.stage_bytes = (A.w_box_off + A.w_box_bytes + 127u) & ~127u;
+    A.chunk_w = P.chunk_w;
+    A.items_per_box = P.items_per_box;
+    long cap = ((1L << 30) - (1L << 20)) / A.items_per_box;
+    if (cap > (1L << 21)) cap = 1L << 21;
+    A.fast_cap = (int)cap;
+    A.fixed_bits = P.fixed_bits;
+    A.vtvg = 1.0 / (6.0 * (double)P.d.n1 * (double)P.d.n2 * (double)P.d.n3);
+    A.omega = omega;
+    int *status = reinterpret_cast<int *>(ws);
+    A.status = status;
+    A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
+    cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);
+    if (e != cudaSuccess) return TETRA_ECUDA;
+    e = (P.d.mode == TETRA_POINT) ? launch_norb<TETRA_POINT>(P, te, tw, A, stream)
+                                  : launch_norb<TETRA_BIN>(P, te, tw, A, stream);
+    if (e != cudaSuccess) return TETRA_ECUDA;
+    const long total = (long)P.d.n_orb * P.d.n_omega;
+    const int rb = 256;
+    const int rg = (int)std::min<long>((total + rb - 1) / rb, 4L * P.sm_count);
+    tetra_dos_reduce_kernel<<<rg, rb, 0, stream>>>(A.G, P.grid_x, P.d.n_orb, P.d.n_omega,
+                                                   P.chunk_w, P.d.mode, omega, A.vtvg,
+                                                   P.fixed_bits, dos);
+    if (cudaGetLastError() != cudaSuccess) return TETRA_ECUDA;
+    return TETRA_OK;
+}
+
+}  // namespace tetra
