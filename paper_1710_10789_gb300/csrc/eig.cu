@@ -32,7 +32,7 @@ template <int N>
 struct Mat {
     float hr[N][N], hi[N][N];   // upper triangle of H used (i <= j)
     float vr[N][N], vi[N][N];   // eigenvectors in columns
-    float skip;                 // couplings below this are dropped (~FP32 rounding of ||H||)
+    float skip;                 // couplings at or below this are dropped unrotated
 };
 
 // Full-matrix element H_kp from upper-triangle storage (k != p).
@@ -124,10 +124,17 @@ __device__ __forceinline__ void jacobi(Mat<N> &M) {
 #pragma unroll
         for (int i = 0; i < N; ++i) fro += M.hr[i][i] * M.hr[i][i];
         fro += 2.f * offdiag2(M);
-        M.skip = 4e-7f * sqrtf(fro) + 1e-30f;
-        // cyclic sweeps until a sweep finds every coupling negligible (at most 12)
-        for (int sweep = 0; sweep < 12; ++sweep)
-            if (!Sweep<N, 0, 1>::run(M)) break;
+        // couplings below the FP32 resolution of ||H|| are dropped unrotated; the
+        // 1e-18 floor keeps |h|^2 out of the denormal range, where |h| (and with
+        // it the phase h*/|h| of the rotation) would lose accuracy
+        M.skip = 6e-8f * sqrtf(fro) + 1e-18f;
+        // cyclic sweeps until the squared off-diagonal norm is below 1e-14 of
+        // ||H||^2 (FP32 rounding level; convergence is quadratic), at most 12
+        const float tol = 1e-14f * fro + 1e-30f;
+        for (int sweep = 0; sweep < 12; ++sweep) {
+            if (offdiag2(M) <= tol) break;
+            Sweep<N, 0, 1>::run(M);
+        }
     }
 }
 
