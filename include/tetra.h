@@ -116,6 +116,29 @@ tetra_status_t tetra_dos(tetra_plan_t plan, const float *eps, const void *w,
                          const float *omega, float *dos, void *ws, size_t ws_bytes,
                          cudaStream_t stream);
 
+/* tetra_dos without a workspace argument, for callers that cannot allocate
+ * device memory where they need a DOS: code under a host framework that owns
+ * all device allocations through its own pool, code whose device-memory budget
+ * is fixed before it starts, or a latency-sensitive loop that must not call
+ * cudaMalloc / cudaFree. The paper has no counterpart; it is a library
+ * convenience.
+ *   Scratch: a static device array of 32 MiB inside libtetra (held on every
+ *   GPU that loads the library until the process exits). The call allocates
+ *   nothing. If the plan's per-CTA partial sums do not fit, fewer persistent
+ *   CTAs are used (same result, bit for bit); if n_orb * n_omega * 8 bytes plus
+ *   256 bytes exceeds 32 MiB even with one CTA, returns TETRA_ENOMEM.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call on a device uses the same array, and the call clears
+ *   what it needs before use. Calls whose kernels overlap on the GPU (different
+ *   streams, or host threads) race on the array and give wrong results;
+ *   serialise them. Device-side status words of this variant are not reported
+ *   (use tetra_dos with a workspace and tetra_workspace_status to diagnose).
+ * Arguments and results are those of tetra_dos. */
+tetra_status_t tetra_dos_noalloc(tetra_plan_t plan, const float *eps, const void *w,
+                                 const float *omega, float *dos, cudaStream_t stream);
+
 /* Adjoint of tetra_dos in TETRA_BIN mode (not in the paper; the derivative of
  * its bin-averaged DOS). Given grad_dos = dL/d dos [n_orb][n_omega], writes
  *   grad_eps = dL/d eps (float, tetra layout, eps_stride)

@@ -23,7 +23,8 @@ __all__ = [
     "TetraError", "TetraDesc", "TetraLayout", "TetraModel", "build", "lib", "lib_path",
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
-    "tetra_workspace_status", "tetra_strerror", "tetra_version", "Plan", "EXPORTED_SYMBOLS",
+    "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc", "Plan",
+    "EXPORTED_SYMBOLS",
 ]
 
 TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
@@ -36,7 +37,7 @@ _MODES = {"point": TETRA_POINT, "bin": TETRA_BIN}
 EXPORTED_SYMBOLS = (
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
-    "tetra_workspace_status", "tetra_strerror", "tetra_version",
+    "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc",
 )
 
 
@@ -94,6 +95,7 @@ def lib():
             L.tetra_workspace_bytes.argtypes = [vp]
             L.tetra_workspace_bytes.restype = sz
             L.tetra_dos.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
+            L.tetra_dos_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
             L.tetra_dos_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
             L.tetra_eig.argtypes = [vp, ctypes.POINTER(TetraModel), vp, vp, vp]
             L.tetra_eig_backward.argtypes = [vp, ctypes.POINTER(TetraModel), vp, vp, vp, vp, sz, vp]
@@ -104,6 +106,7 @@ def lib():
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
             for name in ("tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_dos",
+                         "tetra_dos_noalloc",
                          "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
                          "tetra_workspace_status"):
                 getattr(L, name).restype = i
@@ -139,6 +142,11 @@ def tetra_workspace_bytes(plan: int) -> int:
 
 def tetra_dos(plan, eps, w, omega, dos, ws, ws_bytes, stream) -> int:
     return lib().tetra_dos(plan, eps, w, omega, dos, ws, ws_bytes, stream)
+
+
+def tetra_dos_noalloc(plan, eps, w, omega, dos, stream) -> int:
+    """tetra_dos with the library's fixed scratch instead of a workspace (see tetra.h)."""
+    return lib().tetra_dos_noalloc(plan, eps, w, omega, dos, stream)
 
 
 def tetra_dos_backward(plan, eps, w, omega, grad_dos, grad_eps, grad_w, ws, ws_bytes, stream) -> int:
