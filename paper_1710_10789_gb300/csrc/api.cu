@@ -62,12 +62,14 @@ tetra_status_t encode_point_map(CUtensorMap *map, const void *base, CUtensorMapD
 // Chooses the box shape, energy chunking and grid of the forward kernel.
 static tetra_status_t plan_geometry(Plan &P) {
     const tetra_desc_t &d = P.d;
-    P.BX = std::min(env_int("TETRA_BOX_X", 4), d.n1);
-    P.BY = std::min(env_int("TETRA_BOX_Y", 4), d.n2);
+    // box sides are powers of two (items are decoded with shifts)
+    auto pow2_floor = [](int v) { int p = 1; while (2 * p <= v) p *= 2; return p; };
+    P.BX = pow2_floor(std::max(1, std::min(env_int("TETRA_BOX_X", 4), d.n1)));
+    P.BY = pow2_floor(std::max(1, std::min(env_int("TETRA_BOX_Y", 4), d.n2)));
     // at most ~1536 (tetrahedron, band) items per box keeps the per-item
     // fixed-point cap of the int32 tile (2^30 / items) above typical values
     const int bz_default = std::max(1, std::min(4, 1536 / (96 * d.n_bands)));
-    P.BZ = std::min(env_int("TETRA_BOX_Z", bz_default), P.z1 - P.z0);
+    P.BZ = pow2_floor(std::max(1, std::min(env_int("TETRA_BOX_Z", bz_default), P.z1 - P.z0)));
     if (P.BX < 1 || P.BY < 1 || P.BZ < 1) return TETRA_EINVAL;
     P.nbx = (d.n1 + P.BX - 1) / P.BX;
     P.nby = (d.n2 + P.BY - 1) / P.BY;
@@ -81,7 +83,9 @@ static tetra_status_t plan_geometry(Plan &P) {
     P.tile_stride = tetra::norb_template(d.n_orb) + 1;
     // two TMA stages, per-item sort arrays, histogram, mbarriers, alignment
     // slack and the kernel's static variables
-    const size_t fixed = 2 * stage + 6 * (size_t)P.items_per_box + 16 + 2 * 64 * 4 + 16 + 1024 + 512 + 64;
+    const size_t n_classes = (P.items_per_box + 95) / 96;
+    const size_t fixed = 2 * stage + 7 * (size_t)P.items_per_box + 16 + (2 * 256 + 64 * n_classes) * 4 + 32 +
+                         1024 + 512 + 64;
     // per energy: int tile row, cached energy, 1/width (bin mode), block bound share
     const size_t per_w = 4 * (size_t)(P.tile_stride + 1 + (d.mode == TETRA_BIN ? 1 : 0)) + 1;
     if (fixed + per_w * 64 > P.smem_optin) return TETRA_EUNSUPPORTED;

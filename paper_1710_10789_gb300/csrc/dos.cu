@@ -37,7 +37,8 @@ constexpr int kMagicBits = 0x4B400000;  // bit pattern of kMagic
 constexpr int kThreads = 512;
 constexpr uint32_t kSmemAlign = 1024;
 constexpr unsigned kFlushAt = 1u << 30;
-constexpr int kBuckets = 64;   // window-length classes for grouping items
+constexpr int kKBins = 256;     // window-length histogram bins (K >= 255 share one)
+constexpr int kClassSize = 96;  // items per length class: 3 warps of 32
 
 // Table I, corner labels minus one; label c sits at offset (c&1, (c>>1)&1, (c>>2)&1).
 __constant__ int c_table[6][4] = {{0, 1, 2, 5}, {1, 2, 3, 5}, {0, 2, 4, 5},
@@ -47,6 +48,8 @@ struct FwdArgs {
     int n1, n2, n3, nb, n_orb, n_omega;
     int z0, z1;
     int BX, BY, BZ, nbx, nby, n_boxes;
+    int lbx, lby, lbz;   // log2 of the box sides (powers of two)
+    int n_classes;       // ceil(items_per_box / 96)
     int eps_stride, w_stride;
     uint32_t e_box_bytes, w_box_bytes, w_box_off, stage_bytes;   // w box at stage + w_box_off (128-aligned)
     int chunk_w;
@@ -312,9 +315,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     short *s_lo = reinterpret_cast<short *>(blk_bound + n_blk);      // window start - w0
     unsigned short *s_K = reinterpret_cast<unsigned short *>(s_lo + A.items_per_box);
     unsigned short *s_list = s_K + A.items_per_box;                 // items sorted by K
-    int *hist = reinterpret_cast<int *>(
-        (reinterpret_cast<uintptr_t>(s_list + A.items_per_box) + 15) & ~uintptr_t(15));
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(hist + 2 * kBuckets);
+    unsigned char *s_cls = reinterpret_cast<unsigned char *>(s_list + A.items_per_box);
+    int *khist = reinterpret_cast<int *>(
+        (reinterpret_cast<uintptr_t>(s_cls + A.items_per_box) + 15) & ~uintptr_t(15));
+    int *kcursor = khist + kKBins;           // rank cursors per window length
+    int *chist = kcursor + kKBins;           // (class, row residue) counters
+    int *ccursor = chist + 32 * A.n_classes; // scatter cursors per (class, residue)
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(
+        (reinterpret_cast<uintptr_t>(ccursor + 32 * A.n_classes) + 15) & ~uintptr_t(15));
     __shared__ float red_f[kThreads / 32];
     __shared__ int s_abort, s_active;
 
@@ -368,7 +376,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     const int PX = A.BX + 1, PY = A.BY + 1;
-    const int ncube = A.BX * A.BY * A.BZ;
+    const int ncube = A.BX * A.BY * A.BZ;   // a power of two
+    const int lcube = A.lbx + A.lby + A.lbz;
     long long *Gc = A.G + ((long)chunk * gridDim.x + blockIdx.x) * (long)A.n_orb * A.chunk_w;
 
     // prologue: first two boxes
@@ -388,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int box = blockIdx.x + k * gridDim.x;
         if (box >= A.n_boxes) break;
         const int st = k & 1;
-        if (tid < kBuckets) hist[tid] = 0;
+        for (int i = tid; i < kKBins + 32 * A.n_classes; i += blockDim.x) (i < kKBins ? khist[i] : chist[i - kKBins]) = 0;
         const bool ok = mbar_wait_bounded(&mbar[st], (k >> 1) & 1, A.status);
         if (__syncthreads_or(!ok)) {
             s_abort = 1;
@@ -426,10 +435,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // warp. The integers an item adds do not depend on which thread adds
         // them, so the grouping cannot change the result.
         for (int it = tid; it < A.items_per_box; it += blockDim.x) {
-            const int cube = it % ncube;
-            const int t = (it / ncube) % 6;
-            const int n = it / (6 * ncube);
-            const int cx = cube % A.BX, cy = (cube / A.BX) % A.BY, cz = cube / (A.BX * A.BY);
+            const int cube = it & (ncube - 1);
+            const int rest = it >> lcube;
+            const int t = rest % 6, n = rest / 6;
+            const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
             int K = 0, lo = 0;
             if (gx0 + cx < A.n1 && gy0 + cy < A.n2 && gz0 + cz < A.z1) {
                 float e1 = 3.0e38f, e4 = -3.0e38f;
@@ -447,44 +456,84 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             s_lo[it] = (short)(lo - w0);
             s_K[it] = (unsigned short)K;
-            if (K > 0) atomicAdd(&hist[min(K, kBuckets - 1)], 1);
+            if (K > 0) atomicAdd(&khist[min(K, kKBins - 1)], 1);
         }
         for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
         if ((tid & 31) == 0) red_f[tid >> 5] = bmax;
         __syncthreads();
-        // exclusive scan of the histogram into cursors (one warp)
+        // Items ranked by window length K: exclusive scan of the K histogram
+        // gives each length its first rank; an item's rank = first rank + its
+        // place among items of equal K (atomic cursor; items of equal K are
+        // interchangeable). Rank / 96 is the item's length class.
         if (tid < 32) {
-            int carry = 0;
-            for (int b0 = 0; b0 < kBuckets; b0 += 32) {
-                const int v = hist[b0 + tid];
+            constexpr int PER = kKBins / 32;
+            int v[PER], s = 0;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) { v[j] = khist[tid * PER + j]; s += v[j]; }
+            int x = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (tid >= o) x += y;
+            }
+            int run = x - s;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) { kcursor[tid * PER + j] = run; run += v[j]; }
+            if (tid == 31) s_active = x;
+        }
+        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        if ((tid & 31) == 0) red_f[tid >> 5] = bmax;
+        __syncthreads();
+        for (int it = tid; it < A.items_per_box; it += blockDim.x) {
+            const int K = s_K[it];
+            if (K > 0) {
+                const int rank = atomicAdd(&kcursor[min(K, kKBins - 1)], 1);
+                const int cls = rank / kClassSize;
+                s_cls[it] = (unsigned char)cls;
+                atomicAdd(&chist[cls * 32 + (s_lo[it] & 31)], 1);
+            }
+        }
+        __syncthreads();
+        // residue-major order inside each class
+        {
+            const int lane = tid & 31;
+            for (int c = tid >> 5; c < A.n_classes; c += (int)(blockDim.x >> 5)) {
+                const int v = chist[c * 32 + lane];
                 int x = v;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (tid >= o) x += y;
+                    if (lane >= o) x += y;
                 }
-                hist[kBuckets + b0 + tid] = carry + x - v;
-                carry += __shfl_sync(0xffffffffu, x, 31);
+                ccursor[c * 32 + lane] = c * kClassSize + x - v;
             }
-            if (tid == 0) s_active = carry;
         }
         bmax = 0.f;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) bmax = fmaxf(bmax, red_f[i]);
         __syncthreads();
         for (int it = tid; it < A.items_per_box; it += blockDim.x) {
-            const int K = s_K[it];
-            if (K > 0) s_list[atomicAdd(&hist[kBuckets + min(K, kBuckets - 1)], 1)] = (unsigned short)it;
+            if (s_K[it] > 0)
+                s_list[atomicAdd(&ccursor[s_cls[it] * 32 + (s_lo[it] & 31)], 1)] = (unsigned short)it;
         }
         __syncthreads();
         const int n_active = s_active;
+        const int n_slots = 3 * ((n_active + kClassSize - 1) / kClassSize);
 
-        // Pass B: items in order of window length
-        for (int r = tid; r < n_active; r += blockDim.x) {
-            const int it = s_list[r];
-            const int cube = it % ncube;
-            const int t = (it / ncube) % 6;
-            const int n = it / (6 * ncube);
-            const int cx = cube % A.BX, cy = (cube / A.BX) % A.BY, cz = cube / (A.BX * A.BY);
+        // Pass B: warp g (0..2) of a class takes the class's items g, g+3, g+6, ...
+        // A class holds 96 items of nearly equal window length, so the lanes
+        // finish together; it is residue-major, so the 32 lanes get windows that
+        // start on (nearly) distinct tile rows mod 32 and their shared-memory
+        // atomics hit distinct banks at every step.
+        const int lane = tid & 31;
+        for (int slot = tid >> 5; slot < n_slots; slot += (int)(blockDim.x >> 5)) {
+            const int c = slot / 3;
+            const int pos = c * kClassSize + (slot - 3 * c) + 3 * lane;
+            if (pos >= n_active) continue;
+            const int it = s_list[pos];
+            const int cube = it & (ncube - 1);
+            const int rest = it >> lcube;
+            const int t = rest % 6, n = rest / 6;
+            const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
             float e[4];
             int p[4];
 #pragma unroll
@@ -707,6 +756,8 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
     A.n_omega = P.d.n_omega;
     A.z0 = P.z0; A.z1 = P.z1;
     A.BX = P.BX; A.BY = P.BY; A.BZ = P.BZ; A.nbx = P.nbx; A.nby = P.nby; A.n_boxes = P.n_boxes;
+    A.lbx = __builtin_ctz(P.BX); A.lby = __builtin_ctz(P.BY); A.lbz = __builtin_ctz(P.BZ);
+    A.n_classes = (P.items_per_box + 95) / 96;
     A.eps_stride = P.eps_stride; A.w_stride = P.w_stride;
     const uint32_t npts = (uint32_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
     A.e_box_bytes = npts * P.eps_stride * 4u;
