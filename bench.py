@@ -129,19 +129,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def in_window_count(torch, eps, n, nb, omega, mode):
+def in_window_count(torch, eps, n, nb, omega, mode, zc=16):
     """Exact number of (tetra, band, energy) triples with the energy strictly
-    inside (E1, E4) (point mode) or the bin overlapping it (bin mode)."""
+    inside (E1, E4) (point mode) or the bin overlapping it (bin mode), for an
+    n^3 grid in the tetra layout (zc cube planes at a time)."""
     table = [(0, 1, 2, 5), (1, 2, 3, 5), (0, 2, 4, 5), (2, 3, 5, 7), (2, 4, 5, 6), (2, 5, 6, 7)]
     om = omega.double()
     total = 0
-    for z in range(n):
-        planes = eps[z:z + 2, :, :, :nb].double()  # (2, n+1, n+1, nb)
+    for z0 in range(0, n, zc):
+        nz = min(zc, n - z0)
+        planes = eps[z0:z0 + nz + 1, :, :, :nb].double()  # (nz+1, n+1, n+1, nb)
         for t in table:
             cs = []
             for c in t:
                 dx, dy, dz = c & 1, (c >> 1) & 1, (c >> 2) & 1
-                cs.append(planes[dz, dy:dy + n, dx:dx + n, :])
+                cs.append(planes[dz:dz + nz, dy:dy + n, dx:dx + n, :])
             st = torch.stack(cs, 0)
             e1 = st.min(0).values.reshape(-1)
             e4 = st.max(0).values.reshape(-1)
@@ -155,6 +157,111 @@ def in_window_count(torch, eps, n, nb, omega, mode):
                 hi = hi.clamp(max=om.numel() - 1)
             total += int((hi - lo).clamp(min=0).sum().item())
     return total
+
+
+def alu_roofline(torch, dev, triples, items, ms):
+    """Algorithmic FP32-pipe throughput of the forward kernel against the FP32
+    peak of the GPU (SMs x 128 lanes x 2 flop x max SM clock)."""
+    mp = {}
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = float(mp.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = 2.0 * (OPS_PER_TRIPLE * triples + OPS_PER_ITEM * items)
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "tetra_dos_fwd_kernel", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                           "(sm_max_mhz of measured MEASURED_PEAKS.json)",
+            "algorithmic": f"{OPS_PER_TRIPLE} FMA-pipe ops x {triples} in-window triples + "
+                           f"{OPS_PER_ITEM} x {items} tetra-bands"}
+
+
+def time_dos(torch, plan, eps, w, omega, out, steps, warmup):
+    """Mean ms of the DOS call alone (events on the launching stream)."""
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.dos(eps, w, omega, out=out)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(steps):
+        plan.dos(eps, w, omega, out=out)
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def precision_variants(torch, T, n, nw, mode, params, R, omega, dos32, steps, warmup, local):
+    """Same workload with the orbital weights stored in FP16 / BF16 (FP32
+    arithmetic): DOS time, roofline and the largest deviation from the FP32-weight
+    DOS relative to its maximum."""
+    out = {}
+    for wd in ("f16", "bf16"):
+        plan = T.Plan(n, n, n, 8, 8, nw, mode=mode, weight_dtype=wd, device=local)
+        eps, w = plan.empty_inputs()
+        plan.eig(params, R, eps, w)
+        d = torch.empty_like(dos32)
+        ms = time_dos(torch, plan, eps, w, omega, d, steps, warmup)
+        assert plan.status() == T.TETRA_OK
+        dev_ = float((d - dos32).abs().max() / dos32.abs().max())
+        out[wd] = {"dos_ms": ms, "dense_updates_per_s": 6 * n ** 3 * 8 * nw / (ms * 1e-3),
+                   "weight_bytes": int(w.numel() * w.element_size()),
+                   "max_rel_dev_vs_f32_weights": dev_}
+        del eps, w, plan
+        torch.cuda.empty_cache()
+    return out
+
+
+def batched_workload(torch, T, mode, steps, warmup, local, tune=None, count_window=True):
+    """64 seeded 8-orbital models, cubic grids N ~ U{16..96}, 500-3000 energies
+    over each model's own band window; eigen-data by tetra_eig; all DOS in one
+    graph-captured launch. Returns timing and counts."""
+    import tbgen
+    dev = torch.device("cuda", local)
+    specs = tbgen.batched_problems(64)
+    grids = [(s["n"],) * 3 for s in specs]
+    nws = [s["n_omega"] for s in specs]
+    bplan = T.BatchPlan(grids, nws, 8, 8, mode=mode, tune=tune, device=local)
+    E, W, OM = [], [], []
+    for m, s in enumerate(specs):
+        model = tbgen.tb_model(s["seed"], n_orb=8)
+        p_np, R_np = model_arrays(model)
+        plan = T.Plan(*grids[m], 8, 8, s["n_omega"], mode=mode, device=local)
+        eps, w = plan.eig(torch.from_numpy(p_np).to(dev), torch.from_numpy(R_np).to(dev))
+        torch.cuda.synchronize()
+        lo, hi = float(eps[..., :8].min()) - 0.1, float(eps[..., :8].max()) + 0.1
+        om = tbgen.uniform_grid(lo, hi, s["n_omega"]) if mode == "point" else \
+            tbgen.bin_edges(lo, hi, s["n_omega"])
+        E.append(eps)
+        W.append(w)
+        OM.append(torch.from_numpy(om).to(dev))
+    g, out = bplan.graph(E, W, OM)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    s_ = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s_)
+    for _ in range(steps):
+        g.replay()
+    b.record(s_)
+    torch.cuda.synchronize()
+    assert bplan.status() == T.TETRA_OK
+    ms = a.elapsed_time(b) / steps
+    dense = sum(6 * s["n"] ** 3 * 8 * s["n_omega"] for s in specs)
+    items = sum(6 * s["n"] ** 3 * 8 for s in specs)
+    triples = None
+    if count_window:
+        triples = sum(in_window_count(torch, E[m], specs[m]["n"], 8, OM[m], mode) for m in range(64))
+    return {"ms": ms, "dense": dense, "items": items, "triples": triples, "box": list(bplan.box),
+            "ctas": bplan.grid, "slots": bplan.n_slots, "specs": specs, "E": E, "W": W, "OM": OM,
+            "plan": bplan, "out": out}
 
 
 def cpu_baseline(n, n_omega, seed=0, planes=1, threads=None):
@@ -292,23 +399,7 @@ def main():
         return
     triples = in_window_count(torch, eps, n, 8, omega, args.mode)
     clocks = clk.summary()
-    mp = {}
-    try:
-        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    sm_max = float(mp.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    alg_flops = 2.0 * (OPS_PER_TRIPLE * triples + OPS_PER_ITEM * n_tet * 8)
-    achieved = alg_flops / (dos_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "tetra_dos_fwd_kernel", "achieved": achieved,
-            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-            "traffic": None,
-            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
-                           "(sm_max_mhz of measured MEASURED_PEAKS.json)",
-            "algorithmic": f"{OPS_PER_TRIPLE} FMA-pipe ops x {triples} in-window triples + "
-                           f"{OPS_PER_ITEM} x {n_tet * 8} tetra-bands"}
+    roof = alu_roofline(torch, dev, triples, n_tet * 8, dos_ms)
     # end to end through the public API: host model in, host DOS out
     e2e = None
     if not args.quick:
@@ -333,6 +424,21 @@ def main():
         e2e = {"value": dense / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(p_host.numel() * 4 + R_host.numel() * 4),
                "d2h_bytes_per_step": int(d_host.numel() * 4), "ms_per_step": e2e_ms}
+    variants = None
+    if not args.quick:
+        variants = {"precision": precision_variants(torch, T, n, nw, args.mode, params, R, omega, dos,
+                                                    args.steps, args.warmup, local)}
+        bt = batched_workload(torch, T, args.mode, args.steps, args.warmup, local)
+        variants["batched"] = {
+            "workload": "64 seeded 8-orbital models, N^3 grids N ~ U{16..96}, 500-3000 energies each, "
+                        "FP32, one graph-captured launch (memset + forward + reduce)",
+            "ms_per_launch": bt["ms"], "dense_updates_per_s": bt["dense"] / (bt["ms"] * 1e-3),
+            "in_window_updates_per_s": bt["triples"] / (bt["ms"] * 1e-3),
+            "in_window_triples": bt["triples"], "tetra_bands": bt["items"],
+            "box": bt["box"], "ctas": bt["ctas"], "partial_slots": bt["slots"],
+            "roofline": alu_roofline(torch, dev, bt["triples"], bt["items"], bt["ms"])}
+        del bt
+        torch.cuda.empty_cache()
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(n, nw, seed=0, planes=1)
@@ -352,7 +458,7 @@ def main():
         "in_window_updates_per_s": triples / (dos_ms * 1e-3),
         "dense_updates_per_s_dos_only": dense / (dos_ms * 1e-3),
         "in_window_triples": triples,
-        "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
+        "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks, "variants": variants,
         "gpu_launches": 3 * args.steps,
     }
     print(json.dumps(line), flush=True)

@@ -20,7 +20,7 @@
  *
  * k-grid and the padded point-major layout ("tetra layout")
  *  - The k-grid is periodic and Gamma-centred with n1 x n2 x n3 points,
- *    k = 2 pi (x/n1, y/n2, z/n3) in reciprocal-lattice units (Sec. III.A uses
+ *    k = 2 pi (x/n1, y/n2, z/n3) in reciprocal-lattice units (Sec. IV.A uses
  *    N x N x 10 grids). Every point is the origin of one elemental cube, which
  *    is split into the six tetrahedra of Table I around its 3-6 diagonal; cube
  *    corner label c = 1 + dx + 2 dy + 4 dz for the offset (dx, dy, dz).
@@ -101,7 +101,7 @@ size_t tetra_workspace_bytes(tetra_plan_t plan);
  *   eps, w : band energies and orbital weights in the tetra layout.
  *   omega  : TETRA_POINT: n_omega ascending energies E_i.
  *            TETRA_BIN:   n_omega + 1 ascending bin edges.
- *            Any ascending grid is correct; equidistant grids (Sec. III.A) are
+ *            Any ascending grid is correct; equidistant grids (Sec. IV.A) are
  *            fastest.
  *   dos    : [n_orb][n_omega] float, overwritten.
  *            TETRA_POINT: dos[s][i] = sum_{T,n} sum_l b_{n,l,s} dw_l/dE (E_i).
@@ -145,7 +145,8 @@ tetra_status_t tetra_dos_noalloc(tetra_plan_t plan, const float *eps, const void
  *   grad_w   = dL/d w   (float, tetra layout with w_stride; F32 even when w
  *                        is stored in F16/BF16)
  * Interior points receive the full derivative with respect to the value of
- * that k-point; halo points (x == n1 or y == n2 or z == n3) are set to 0.
+ * that k-point; halo points (x == n1 or y == n2 or z == n3) and the layout's
+ * padding entries are set to 0 (both arrays are overwritten completely).
  * Returns TETRA_EUNSUPPORTED for a TETRA_POINT plan. */
 tetra_status_t tetra_dos_backward(tetra_plan_t plan, const float *eps, const void *w,
                                   const float *omega, const float *grad_dos,
@@ -168,7 +169,9 @@ typedef struct {
  * grid (Sec. II.A: diagonalisation of H(k) point by point), written directly
  * in the tetra layout. A batched cyclic Jacobi eigensolver on the GPU; bands
  * ascending, w[n][s] = |V_{s n}|^2 stored in the plan's weight_dtype.
- * Requires plan n_bands == model n_orb <= 8. Halo points are written too. */
+ * Requires plan n_bands == model n_orb <= 8. Halo points are written too. For
+ * a slab plan (z_begin, z_end) only the point planes z_begin .. z_end (the
+ * corners of its cubes) are written; the rest of eps and w is left as is. */
 tetra_status_t tetra_eig(tetra_plan_t plan, const tetra_model_t *model, float *eps, void *w,
                          cudaStream_t stream);
 
@@ -182,6 +185,61 @@ tetra_status_t tetra_eig_backward(tetra_plan_t plan, const tetra_model_t *model,
                                   float *grad_params, void *ws, size_t ws_bytes,
                                   cudaStream_t stream);
 size_t tetra_eig_workspace_bytes(tetra_plan_t plan, int n_R);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent DOS problems in ONE launch of the forward kernel (not in
+ * the paper, which evaluates one model at a time; Secs. III-IV). Each model has its
+ * own k-grid, energy grid and data; all share n_bands, n_orb, mode and
+ * weight_dtype. The persistent CTAs take contiguous ranges of (model, box)
+ * work of equal estimated cost; per-model results are summed from exact
+ * integer partials, so each model's DOS equals what tetra_dos gives for it up
+ * to the fixed-point rounding of its own plan (bit-identical when both use the
+ * same box shape and fixed-point bits).
+ * Every argument of tetra_dos_batched travels in kernel parameters, so the
+ * call can be captured in a CUDA graph and replayed with the same pointers. */
+#define TETRA_MAX_BATCH 64
+
+typedef struct tetra_batch_plan_s *tetra_batch_plan_t;
+
+/* Launch-shape choices (e.g. from an autotuner); zero fields take the default. */
+typedef struct {
+    int box_x, box_y, box_z; /* cubes per box side (rounded down to powers of two
+                                and clipped to the smallest grid); default 4,4,2
+                                for 8 bands                                        */
+    int ctas_per_sm;         /* persistent CTAs per SM, default 1                  */
+    float item_cost;         /* schedule cost of one item's fixed work, in units of
+                                one energy step; default 3                         */
+} tetra_tune_t;
+
+/* Plans a batch of n_models (1..TETRA_MAX_BATCH) descriptions (host array).
+ * tune may be NULL. Returns TETRA_EINVAL if the descriptions differ in n_bands,
+ * n_orb, mode or weight_dtype or one is invalid, TETRA_EUNSUPPORTED if the
+ * largest n_omega does not fit one shared-memory tile (about 4100 energies, or
+ * 3700 bins, for 8 orbitals and 8 bands in F32 with the default box). The plan
+ * owns only host memory. */
+tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *descs, int n_models,
+                                  const tetra_tune_t *tune, int device);
+tetra_status_t tetra_batch_plan_destroy(tetra_batch_plan_t plan);
+
+/* Layout strides of model `model` (host call). */
+tetra_status_t tetra_batch_layout(tetra_batch_plan_t plan, int model, tetra_layout_t *layout);
+
+/* Bytes of device workspace tetra_dos_batched needs (host call). */
+size_t tetra_batch_workspace_bytes(tetra_batch_plan_t plan);
+
+/* Chosen launch shape (host call): box[3] cubes per box side, grid = persistent
+ * CTAs, n_slots = int64 partial tiles. Any output pointer may be NULL. */
+tetra_status_t tetra_batch_info(tetra_batch_plan_t plan, int *box, int *grid, int *n_slots);
+
+/* DOS of every model of the batch (Sec. II.C, Eqs. (8)-(9), as tetra_dos).
+ *   eps, w, omega, dos: HOST arrays of n_models DEVICE pointers; model m uses
+ *   eps[m], w[m] in its tetra layout, omega[m] (n_omega or n_omega + 1 values)
+ *   and writes dos[m] ([n_orb][n_omega] of its description).
+ *   ws: at least tetra_batch_workspace_bytes(plan) bytes, 16-byte aligned.
+ * The host arrays are read during the call only. */
+tetra_status_t tetra_dos_batched(tetra_batch_plan_t plan, const float *const *eps, const void *const *w,
+                                 const float *const *omega, float *const *dos, void *ws,
+                                 size_t ws_bytes, cudaStream_t stream);
 
 /* Device-side status recorded in a workspace by the last call that used it
  * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. */

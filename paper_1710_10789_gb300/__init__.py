@@ -24,7 +24,9 @@ __all__ = [
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc", "Plan",
-    "EXPORTED_SYMBOLS",
+    "EXPORTED_SYMBOLS", "TetraTune", "tetra_plan_batched", "tetra_batch_plan_destroy",
+    "tetra_batch_layout", "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
+    "BatchPlan", "TETRA_MAX_BATCH",
 ]
 
 TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
@@ -38,7 +40,10 @@ EXPORTED_SYMBOLS = (
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc",
+    "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
+    "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
 )
+TETRA_MAX_BATCH = 64
 
 
 class TetraError(RuntimeError):
@@ -59,6 +64,11 @@ class TetraLayout(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("eps_stride", ctypes.c_int), ("w_stride", ctypes.c_int),
                 ("eps_elems", ctypes.c_size_t), ("w_elems", ctypes.c_size_t)]
+
+
+class TetraTune(ctypes.Structure):
+    _fields_ = [("box_x", ctypes.c_int), ("box_y", ctypes.c_int), ("box_z", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("item_cost", ctypes.c_float)]
 
 
 class TetraModel(ctypes.Structure):
@@ -102,13 +112,24 @@ def lib():
             L.tetra_eig_workspace_bytes.argtypes = [vp, i]
             L.tetra_eig_workspace_bytes.restype = sz
             L.tetra_workspace_status.argtypes = [vp, vp]
+            L.tetra_plan_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(TetraDesc), i,
+                                             ctypes.POINTER(TetraTune), i]
+            L.tetra_batch_plan_destroy.argtypes = [vp]
+            L.tetra_batch_layout.argtypes = [vp, i, ctypes.POINTER(TetraLayout)]
+            L.tetra_batch_workspace_bytes.argtypes = [vp]
+            L.tetra_batch_workspace_bytes.restype = sz
+            L.tetra_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+            L.tetra_dos_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                            ctypes.POINTER(vp), ctypes.POINTER(vp), vp, sz, vp]
             L.tetra_strerror.argtypes = [i]
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
             for name in ("tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_dos",
                          "tetra_dos_noalloc",
                          "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
-                         "tetra_workspace_status"):
+                         "tetra_workspace_status", "tetra_plan_batched",
+                         "tetra_batch_plan_destroy", "tetra_batch_layout", "tetra_batch_info",
+                         "tetra_dos_batched"):
                 getattr(L, name).restype = i
             _LIB = L
     return _LIB
@@ -170,6 +191,45 @@ def tetra_eig_workspace_bytes(plan, n_R: int) -> int:
 
 def tetra_workspace_status(ws, stream) -> int:
     return lib().tetra_workspace_status(ws, stream)
+
+
+def tetra_plan_batched(descs, tune: "TetraTune | None" = None, device: int = 0) -> int:
+    arr = (TetraDesc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(lib().tetra_plan_batched(ctypes.byref(h), arr, len(descs),
+                                    ctypes.byref(tune) if tune is not None else None, int(device)),
+           "tetra_plan_batched")
+    return h.value
+
+
+def tetra_batch_plan_destroy(plan: int) -> int:
+    return lib().tetra_batch_plan_destroy(plan)
+
+
+def tetra_batch_layout(plan: int, model: int) -> TetraLayout:
+    L = TetraLayout()
+    _check(lib().tetra_batch_layout(plan, int(model), ctypes.byref(L)), "tetra_batch_layout")
+    return L
+
+
+def tetra_batch_workspace_bytes(plan: int) -> int:
+    return int(lib().tetra_batch_workspace_bytes(plan))
+
+
+def tetra_batch_info(plan: int):
+    """(box (bx, by, bz), persistent CTAs, partial slots) chosen by the plan."""
+    box = (ctypes.c_int * 3)()
+    grid, slots = ctypes.c_int(), ctypes.c_int()
+    _check(lib().tetra_batch_info(plan, box, ctypes.byref(grid), ctypes.byref(slots)),
+           "tetra_batch_info")
+    return tuple(box), grid.value, slots.value
+
+
+def tetra_dos_batched(plan, eps, w, omega, dos, ws, ws_bytes, stream) -> int:
+    """eps, w, omega, dos: sequences of device pointers (one per model)."""
+    n = len(eps)
+    arrs = [(ctypes.c_void_p * n)(*[int(x) for x in a]) for a in (eps, w, omega, dos)]
+    return lib().tetra_dos_batched(plan, *arrs, ws, ws_bytes, stream)
 
 
 def tetra_strerror(status: int) -> str:
@@ -287,6 +347,98 @@ class Plan:
         _check(tetra_eig_backward(self.handle, m, _ptr(grad_eps), _ptr(grad_w), _ptr(g), _ptr(ws),
                                   ws.numel(), _stream_handle(stream)), "tetra_eig_backward")
         return g
+
+    def status(self, stream=None) -> int:
+        ws = self.workspace()
+        return tetra_workspace_status(_ptr(ws), _stream_handle(stream))
+
+
+class BatchPlan:
+    """Many independent DOS problems (same n_bands, n_orb, mode, weight dtype) in
+    one launch; ``graph()`` captures that launch in a CUDA graph."""
+
+    def __init__(self, grids, n_omegas, n_bands, n_orb, mode="point", weight_dtype="f32",
+                 tune=None, device=None):
+        torch = _torch()
+        if len(grids) != len(n_omegas):
+            raise ValueError("one energy count per grid")
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.descs = [TetraDesc(int(g[0]), int(g[1]), int(g[2]), n_bands, n_orb, int(nw), _MODES[mode],
+                                _DTYPES[weight_dtype], 0, 0) for g, nw in zip(grids, n_omegas)]
+        self.mode = mode
+        self.weight_dtype = weight_dtype
+        self.device = dev
+        self.tune = tune
+        t = None
+        if tune is not None:
+            t = TetraTune(*[int(x) for x in tune.get("box", (0, 0, 0))], int(tune.get("ctas_per_sm", 0)),
+                          float(tune.get("item_cost", 0.0)))
+        with torch.cuda.device(dev):
+            self.handle = tetra_plan_batched(self.descs, t, dev)
+        self.layouts = [tetra_batch_layout(self.handle, m) for m in range(len(self.descs))]
+        self.workspace_bytes = tetra_batch_workspace_bytes(self.handle)
+        self.box, self.grid, self.n_slots = tetra_batch_info(self.handle)
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _LIB is not None:
+            _LIB.tetra_batch_plan_destroy(h)
+            self.handle = None
+
+    def __len__(self):
+        return len(self.descs)
+
+    @property
+    def torch_weight_dtype(self):
+        torch = _torch()
+        return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.weight_dtype]
+
+    def empty_inputs(self, m):
+        torch = _torch()
+        L = self.layouts[m]
+        dev = torch.device("cuda", self.device)
+        eps = torch.zeros((L.nz, L.ny, L.nx, L.eps_stride), dtype=torch.float32, device=dev)
+        w = torch.zeros((L.nz, L.ny, L.nx, L.w_stride), dtype=self.torch_weight_dtype, device=dev)
+        return eps, w
+
+    def workspace(self):
+        torch = _torch()
+        if self._ws is None:
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8,
+                                   device=torch.device("cuda", self.device))
+        return self._ws
+
+    def empty_outputs(self):
+        torch = _torch()
+        dev = torch.device("cuda", self.device)
+        return [torch.empty((d.n_orb, d.n_omega), dtype=torch.float32, device=dev) for d in self.descs]
+
+    def dos(self, eps, w, omega, out=None, stream=None):
+        if out is None:
+            out = self.empty_outputs()
+        ws = self.workspace()
+        _check(tetra_dos_batched(self.handle, [_ptr(x) for x in eps], [_ptr(x) for x in w],
+                                 [_ptr(x) for x in omega], [_ptr(x) for x in out], _ptr(ws),
+                                 ws.numel(), _stream_handle(stream)), "tetra_dos_batched")
+        return out
+
+    def graph(self, eps, w, omega, out=None):
+        """Captures one batched DOS launch (memset, forward kernel, reduce) over
+        these tensors in a CUDA graph. Returns (graph, out): ``graph.replay()``
+        recomputes ``out`` from the current contents of the inputs."""
+        torch = _torch()
+        if out is None:
+            out = self.empty_outputs()
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.dos(eps, w, omega, out)   # loads the kernels before capture
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.dos(eps, w, omega, out)
+        return g, out
 
     def status(self, stream=None) -> int:
         ws = self.workspace()

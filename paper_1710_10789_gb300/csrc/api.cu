@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -59,17 +60,28 @@ tetra_status_t encode_point_map(CUtensorMap *map, const void *base, CUtensorMapD
     return r == CUDA_SUCCESS ? TETRA_OK : TETRA_EINVAL;
 }
 
-// Chooses the box shape, energy chunking and grid of the forward kernel.
-static tetra_status_t plan_geometry(Plan &P) {
+int pow2_floor(int v) {
+    int p = 1;
+    while (2 * p <= v) p *= 2;
+    return p;
+}
+
+// Default box of cubes for a band count: 4 x 4 x BZ with at most ~1536
+// (tetrahedron, band) items per box, which keeps the per-item fixed-point cap
+// of the int32 tile (2^30 / items) above typical values.
+void default_box(const tetra_desc_t &d, int box[3]) {
+    box[0] = env_int("TETRA_BOX_X", 4);
+    box[1] = env_int("TETRA_BOX_Y", 4);
+    box[2] = env_int("TETRA_BOX_Z", std::max(1, std::min(4, 1536 / (96 * std::max(1, d.n_bands)))));
+}
+
+// Chooses the box shape, energy chunking and grid of the forward kernel. Box
+// sides are powers of two (items are decoded with shifts), clipped to the grid.
+static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) {
     const tetra_desc_t &d = P.d;
-    // box sides are powers of two (items are decoded with shifts)
-    auto pow2_floor = [](int v) { int p = 1; while (2 * p <= v) p *= 2; return p; };
-    P.BX = pow2_floor(std::max(1, std::min(env_int("TETRA_BOX_X", 4), d.n1)));
-    P.BY = pow2_floor(std::max(1, std::min(env_int("TETRA_BOX_Y", 4), d.n2)));
-    // at most ~1536 (tetrahedron, band) items per box keeps the per-item
-    // fixed-point cap of the int32 tile (2^30 / items) above typical values
-    const int bz_default = std::max(1, std::min(4, 1536 / (96 * d.n_bands)));
-    P.BZ = pow2_floor(std::max(1, std::min(env_int("TETRA_BOX_Z", bz_default), P.z1 - P.z0)));
+    P.BX = pow2_floor(std::max(1, std::min(box[0], d.n1)));
+    P.BY = pow2_floor(std::max(1, std::min(box[1], d.n2)));
+    P.BZ = pow2_floor(std::max(1, std::min(box[2], P.z1 - P.z0)));
     if (P.BX < 1 || P.BY < 1 || P.BZ < 1) return TETRA_EINVAL;
     P.nbx = (d.n1 + P.BX - 1) / P.BX;
     P.nby = (d.n2 + P.BY - 1) / P.BY;
@@ -94,7 +106,7 @@ static tetra_status_t plan_geometry(Plan &P) {
     P.chunk_w = (d.n_omega + P.n_chunks - 1) / P.n_chunks;
     P.smem_bytes = fixed + per_w * P.chunk_w + 8;
     P.threads = 512;
-    const int ctas = std::max(1, env_int("TETRA_CTAS_PER_SM", 1)) * P.sm_count;
+    const int ctas = std::max(1, ctas_per_sm) * P.sm_count;
     P.grid_x = std::max(1, std::min(P.n_boxes, (ctas + P.n_chunks - 1) / P.n_chunks));
     // Fixed-point fraction bits. A DOS value is a sum of N contributions of
     // size ~2^F / K units (K = energies per tetrahedron window), each rounded
@@ -112,16 +124,8 @@ static tetra_status_t plan_geometry(Plan &P) {
     return TETRA_OK;
 }
 
-}  // namespace tetra
-
-using tetra::Plan;
-
-extern "C" {
-
-tetra_status_t tetra_plan(tetra_plan_t *plan, const tetra_desc_t *desc, int device) {
-    if (!plan || !desc) return TETRA_EINVAL;
-    *plan = nullptr;
-    const tetra_desc_t &d = *desc;
+// Validates a description and fills a plan for it (box shape given).
+tetra_status_t plan_init(Plan &P, const tetra_desc_t &d, int device, const int box[3], int ctas_per_sm) {
     if (d.n1 < 1 || d.n2 < 1 || d.n3 < 1 || d.n1 > 4096 || d.n2 > 4096 || d.n3 > 4096)
         return TETRA_EINVAL;
     if (d.n_bands < 1 || d.n_bands > 64 || d.n_orb < 1 || d.n_orb > 16 || d.n_omega < 1)
@@ -132,34 +136,44 @@ tetra_status_t tetra_plan(tetra_plan_t *plan, const tetra_desc_t *desc, int devi
     int z0 = d.z_begin, z1 = d.z_end;
     if (z0 == 0 && z1 == 0) z1 = d.n3;
     if (z0 < 0 || z1 > d.n3 || z0 >= z1) return TETRA_EINVAL;
-    Plan *P = new (std::nothrow) Plan();
-    if (!P) return TETRA_ENOMEM;
-    P->d = d;
-    P->device = device;
-    P->z0 = z0;
-    P->z1 = z1;
-    P->nx = d.n1 + 1;
-    P->ny = d.n2 + 1;
-    P->nz = d.n3 + 1;
-    P->wbytes = d.weight_dtype == TETRA_F32 ? 4 : 2;
-    P->eps_stride = tetra::round_up(d.n_bands, 4);
-    const int align = 16 / P->wbytes;
-    int ws = tetra::round_up(d.n_bands * d.n_orb, align);
-    if ((ws * P->wbytes) % 128 == 0) ws += align;   // spread points over smem banks
-    P->w_stride = ws;
-    if (P->w_stride > 256 || P->eps_stride > 256) {
-        delete P;
-        return TETRA_EUNSUPPORTED;
-    }
+    P = Plan();
+    P.d = d;
+    P.device = device;
+    P.z0 = z0;
+    P.z1 = z1;
+    P.nx = d.n1 + 1;
+    P.ny = d.n2 + 1;
+    P.nz = d.n3 + 1;
+    P.wbytes = d.weight_dtype == TETRA_F32 ? 4 : 2;
+    P.eps_stride = round_up(d.n_bands, 4);
+    const int align = 16 / P.wbytes;
+    int ws = round_up(d.n_bands * d.n_orb, align);
+    if ((ws * P.wbytes) % 128 == 0) ws += align;   // spread points over smem banks
+    P.w_stride = ws;
+    if (P.w_stride > 256 || P.eps_stride > 256) return TETRA_EUNSUPPORTED;
     int sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
-        delete P;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
         return TETRA_ECUDA;
-    }
-    P->sm_count = sms;
-    P->smem_optin = (size_t)optin;
-    tetra_status_t st = tetra::plan_geometry(*P);
+    P.sm_count = sms;
+    P.smem_optin = (size_t)optin;
+    return plan_geometry(P, box, ctas_per_sm);
+}
+
+}  // namespace tetra
+
+using tetra::Plan;
+
+extern "C" {
+
+tetra_status_t tetra_plan(tetra_plan_t *plan, const tetra_desc_t *desc, int device) {
+    if (!plan || !desc) return TETRA_EINVAL;
+    *plan = nullptr;
+    int box[3];
+    tetra::default_box(*desc, box);
+    Plan *P = new (std::nothrow) Plan();
+    if (!P) return TETRA_ENOMEM;
+    tetra_status_t st = tetra::plan_init(*P, *desc, device, box, tetra::env_int("TETRA_CTAS_PER_SM", 1));
     if (st != TETRA_OK) {
         delete P;
         return st;
@@ -236,6 +250,150 @@ tetra_status_t tetra_eig_backward(tetra_plan_t plan, const tetra_model_t *model,
     if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
     return tetra::launch_eig_backward(*plan, model, grad_eps, grad_w, grad_params, ws, ws_bytes,
                                       stream);
+}
+
+tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *descs, int n_models,
+                                  const tetra_tune_t *tune, int device) {
+    if (!plan || !descs) return TETRA_EINVAL;
+    *plan = nullptr;
+    if (n_models < 1 || n_models > tetra::kMaxBatch) return TETRA_EINVAL;
+    const tetra_desc_t &d0 = descs[0];
+    for (int m = 1; m < n_models; ++m) {
+        const tetra_desc_t &d = descs[m];
+        if (d.n_bands != d0.n_bands || d.n_orb != d0.n_orb || d.mode != d0.mode ||
+            d.weight_dtype != d0.weight_dtype)
+            return TETRA_EINVAL;
+    }
+    tetra_tune_t t = {0, 0, 0, 0, 0.f};
+    if (tune) t = *tune;
+    int box[3];
+    tetra::default_box(d0, box);
+    if (t.box_x > 0) box[0] = t.box_x;
+    if (t.box_y > 0) box[1] = t.box_y;
+    if (t.box_z > 0) box[2] = t.box_z;
+    // one box shape for the whole batch: clipped to the smallest grid
+    for (int m = 0; m < n_models; ++m) {
+        const tetra_desc_t &d = descs[m];
+        if (d.n1 < 1 || d.n2 < 1 || d.n3 < 1) return TETRA_EINVAL;
+        const int zb = d.z_begin, ze = (d.z_begin == 0 && d.z_end == 0) ? d.n3 : d.z_end;
+        box[0] = std::min(box[0], d.n1);
+        box[1] = std::min(box[1], d.n2);
+        box[2] = std::min(box[2], std::max(1, ze - zb));
+    }
+    for (int i = 0; i < 3; ++i) box[i] = tetra::pow2_floor(std::max(1, box[i]));
+    const int ctas_per_sm = t.ctas_per_sm > 0 ? t.ctas_per_sm : 1;
+    const double item_cost = t.item_cost > 0.f ? (double)t.item_cost : 3.0;
+    tetra_batch_plan_s *B = new (std::nothrow) tetra_batch_plan_s();
+    if (!B) return TETRA_ENOMEM;
+    auto fail = [&](tetra_status_t s) {
+        delete B;
+        return s;
+    };
+    B->n_models = n_models;
+    B->device = device;
+    B->big = 0;
+    for (int m = 0; m < n_models; ++m) {
+        tetra_status_t st = tetra::plan_init(B->models[m], descs[m], device, box, ctas_per_sm);
+        if (st != TETRA_OK) return fail(st);
+        if (descs[m].n_omega > descs[B->big].n_omega) B->big = m;
+    }
+    // the largest energy grid must fit one shared tile (no energy chunks)
+    const Plan &Pb = B->models[B->big];
+    if (Pb.n_chunks != 1) return fail(TETRA_EUNSUPPORTED);
+    B->chunk_w = Pb.chunk_w;
+    B->smem_bytes = Pb.smem_bytes;
+    // Static schedule. Estimated cost of a box of model m: its items, each with
+    // a fixed part (corner loads, sort, window, set-up; item_cost energy-steps)
+    // and its window, about 0.72 n_omega h energies for an energy grid that
+    // spans the bands (h = mean 1/n of the grid; measured on the tight-binding
+    // models). Contiguous ranges of (model, box) work of equal estimated cost
+    // go to the persistent CTAs in model order.
+    long total_boxes = 0;
+    std::vector<double> cost(n_models);
+    double total = 0.0;
+    for (int m = 0; m < n_models; ++m) {
+        const Plan &P = B->models[m];
+        const double h = (1.0 / P.d.n1 + 1.0 / P.d.n2 + 1.0 / P.d.n3) / 3.0;
+        cost[m] = (double)P.items_per_box * (item_cost + 0.72 * P.d.n_omega * h);
+        B->box_base[m] = (int)total_boxes;
+        total_boxes += P.n_boxes;
+        total += cost[m] * P.n_boxes;
+        if (total_boxes > (1L << 30)) return fail(TETRA_EUNSUPPORTED);
+    }
+    const int G = (int)std::max<long>(1, std::min<long>({total_boxes, (long)ctas_per_sm * Pb.sm_count,
+                                                         (long)tetra::kMaxBatchCtas}));
+    B->grid_x = G;
+    {
+        int c = 0;
+        double acc = 0.0;
+        long g = 0;
+        B->cta_begin[0] = 0;
+        for (int m = 0; m < n_models; ++m) {
+            for (int b = 0; b < B->models[m].n_boxes; ++b) {
+                acc += cost[m];
+                ++g;
+                while (c + 1 < G && acc >= total * (double)(c + 1) / G) B->cta_begin[++c] = (int)g;
+            }
+        }
+        while (c < G) B->cta_begin[++c] = (int)total_boxes;
+    }
+    // partial-sum slots: one per (model, CTA holding boxes of it)
+    int slots = 0;
+    for (int m = 0; m < n_models; ++m) {
+        const int first = B->box_base[m], last = first + B->models[m].n_boxes - 1;
+        int lo = 0;
+        while (B->cta_begin[lo + 1] <= first) ++lo;
+        int hi = lo;
+        while (B->cta_begin[hi + 1] <= last) ++hi;
+        B->c_lo[m] = lo;
+        B->n_pairs[m] = hi - lo + 1;
+        B->pair_base[m] = slots;
+        slots += hi - lo + 1;
+    }
+    B->n_slots = slots;
+    *plan = B;
+    return TETRA_OK;
+}
+
+tetra_status_t tetra_batch_plan_destroy(tetra_batch_plan_t plan) {
+    delete plan;
+    return TETRA_OK;
+}
+
+tetra_status_t tetra_batch_layout(tetra_batch_plan_t plan, int model, tetra_layout_t *layout) {
+    if (!plan || model < 0 || model >= plan->n_models) return TETRA_EINVAL;
+    return tetra_layout(&plan->models[model], layout);
+}
+
+size_t tetra_batch_workspace_bytes(tetra_batch_plan_t plan) {
+    if (!plan) return 0;
+    return tetra::dos_batched_workspace(*plan);
+}
+
+tetra_status_t tetra_batch_info(tetra_batch_plan_t plan, int *box, int *grid, int *n_slots) {
+    if (!plan) return TETRA_EINVAL;
+    if (box) {
+        box[0] = plan->models[0].BX;
+        box[1] = plan->models[0].BY;
+        box[2] = plan->models[0].BZ;
+    }
+    if (grid) *grid = plan->grid_x;
+    if (n_slots) *n_slots = plan->n_slots;
+    return TETRA_OK;
+}
+
+tetra_status_t tetra_dos_batched(tetra_batch_plan_t plan, const float *const *eps, const void *const *w,
+                                 const float *const *omega, float *const *dos, void *ws,
+                                 size_t ws_bytes, cudaStream_t stream) {
+    if (!plan || !eps || !w || !omega || !dos || !ws) return TETRA_EINVAL;
+    if (!tetra::aligned16(ws)) return TETRA_EINVAL;
+    for (int m = 0; m < plan->n_models; ++m) {
+        if (!eps[m] || !w[m] || !omega[m] || !dos[m]) return TETRA_EINVAL;
+        if (!tetra::aligned16(eps[m]) || !tetra::aligned16(w[m])) return TETRA_EINVAL;
+    }
+    if (ws_bytes < tetra::dos_batched_workspace(*plan)) return TETRA_ENOMEM;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    return tetra::launch_dos_batched(*plan, eps, w, omega, dos, ws, ws_bytes, stream);
 }
 
 tetra_status_t tetra_workspace_status(const void *ws, cudaStream_t stream) {

@@ -3,10 +3,14 @@
 //
 // Work decomposition
 //  * The cube grid [0,n1) x [0,n2) x [z0,z1) is cut into boxes of BX*BY*BZ
-//    cubes. A persistent CTA takes boxes blockIdx.x, blockIdx.x + gridDim.x, ...
-//    and, for each, has the box's (BX+1)(BY+1)(BZ+1) corner points of all
-//    bands (energies and orbital weights, tetra layout) copied into shared
-//    memory by two 4-D TMA loads, double buffered across boxes.
+//    cubes. A persistent CTA walks a sequence of boxes and, for each, has the
+//    box's (BX+1)(BY+1)(BZ+1) corner points of all bands (energies and orbital
+//    weights, tetra layout) copied into shared memory by two 4-D TMA loads,
+//    double buffered across boxes. One model: boxes blockIdx.x, blockIdx.x +
+//    gridDim.x, ... (blockIdx.y = energy chunk). A batch of models: a
+//    contiguous range of (model, box) work, cut by the host into ranges of
+//    equal estimated cost; when the model changes the CTA flushes its tile to
+//    the previous model's partial slot and reloads the energy grid.
 //  * One thread handles one (tetrahedron, band) item: it reads the four corner
 //    energies, sorts them with a 5-comparator network carrying the corner
 //    positions (Sec. II.C sorts E1 <= E2 <= E3 <= E4), reads the orbital
@@ -25,7 +29,12 @@
 //    global integer path for rare near-flat tetrahedra. The sum of q_max over
 //    processed items bounds every tile entry; the tile is flushed into the
 //    CTA's int64 partial in global memory before it could overflow.
-//  * tetra_dos_reduce sums the per-CTA int64 partials (exact) and scales by u.
+//  * tetra_dos_reduce sums the per-CTA int64 partials (exact) and scales by u;
+//    for a batch, each model sums the slots of the CTAs that held its boxes.
+#include <atomic>
+#include <memory>
+#include <new>
+
 #include "tetra_internal.cuh"
 
 namespace tetra {
@@ -44,21 +53,18 @@ constexpr int kClassSize = 96;  // items per length class: 3 warps of 32
 __constant__ int c_table[6][4] = {{0, 1, 2, 5}, {1, 2, 3, 5}, {0, 2, 4, 5},
                                   {2, 3, 5, 7}, {2, 4, 5, 6}, {2, 5, 6, 7}};
 
+// Launch constants shared by every model of a launch.
 struct FwdArgs {
-    int n1, n2, n3, nb, n_orb, n_omega;
-    int z0, z1;
-    int BX, BY, BZ, nbx, nby, n_boxes;
+    int nb, n_orb;
+    int BX, BY, BZ;
     int lbx, lby, lbz;   // log2 of the box sides (powers of two)
     int n_classes;       // ceil(items_per_box / 96)
     int eps_stride, w_stride;
     uint32_t e_box_bytes, w_box_bytes, w_box_off, stage_bytes;   // w box at stage + w_box_off (128-aligned)
-    int chunk_w;
+    int chunk_w;         // energies per shared tile (largest model of a batch)
     int items_per_box;
     int fast_cap;
-    int fixed_bits;
-    double vtvg;
-    const float *omega;
-    long long *G;   // [n_chunks][grid_x][n_orb][chunk_w]
+    long long *G;        // int64 partials, [slot][n_orb][chunk_w]
     int *status;
 };
 
@@ -291,10 +297,33 @@ __device__ __forceinline__ void load_weights(const WT *src, int n_orb, float (&b
     }
 }
 
-template <int NORB, typename WT, int MODE>
+// One model of a launch: grid, energy grid and where its partial sums go.
+struct ModelP {
+    int n1, n2, n3, z0, z1, nbx, nby, n_boxes, n_omega;
+    int fixed_bits;
+    int box_base;    // first global work index of the model (batched launches)
+    int pair_base;   // first partial-sum slot of the model (batched launches)
+    int c_lo;        // first CTA whose work range holds boxes of the model (batched)
+    double vtvg;
+    const float *omega;
+};
+
+struct MapPair {   // CUtensorMap is 128-byte aligned
+    CUtensorMap e, w;
+};
+
+// Per-launch model table, passed by value (kernel parameter space).
+template <int MAXM>
+struct Batch {
+    MapPair maps[MAXM];
+    ModelP m[MAXM];
+    int n_models;
+    int cta_begin[MAXM > 1 ? kMaxBatchCtas + 1 : 1];   // batched: CTA c takes global work [cta_begin[c], cta_begin[c+1])
+};
+
+template <int NORB, typename WT, int MODE, int MAXM>
 __global__ void __launch_bounds__(kThreads, 1)
-    tetra_dos_fwd_kernel(const __grid_constant__ CUtensorMap tm_eps,
-                         const __grid_constant__ CUtensorMap tm_w, const FwdArgs A) {
+    tetra_dos_fwd_kernel(const __grid_constant__ Batch<MAXM> B, const FwdArgs A) {
     constexpr int TS = NORB + 1;   // tile row: NORB orbitals + 1 pad (spreads banks)
     extern __shared__ unsigned char smem_raw[];
     // TMA destinations need an aligned base; the dynamic area starts after the
@@ -302,9 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *smem = smem_raw + ((kSmemAlign - (smem_u32(smem_raw) & (kSmemAlign - 1))) &
                                       (kSmemAlign - 1));
     const int tid = threadIdx.x;
-    const int chunk = blockIdx.y;
-    const int w0 = chunk * A.chunk_w;
-    const int wc = min(A.chunk_w, A.n_omega - w0);
+    const int chunk = blockIdx.y;   // energy chunk (single-model launches)
     // shared memory carve-up
     unsigned char *stage[2] = {smem, smem + A.stage_bytes};
     int *tile = reinterpret_cast<int *>(smem + 2 * A.stage_bytes);   // [chunk_w][TS]
@@ -338,64 +365,109 @@ __global__ void __launch_bounds__(kThreads, 1)
             return;
         }
     }
-    for (int i = tid; i < TS * A.chunk_w; i += blockDim.x) tile[i] = 0;
-    for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
-    const int n_om = (MODE == TETRA_POINT) ? wc : wc + 1;
-    for (int i = tid; i < n_om; i += blockDim.x) om[i] = A.omega[w0 + i];
     if (tid == 0) {
         s_abort = 0;
-        prefetch_tensormap(&tm_eps);
-        prefetch_tensormap(&tm_w);
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    if (MODE == TETRA_BIN)
-        for (int i = tid; i < wc; i += blockDim.x) iw[i] = 1.0f / (om[i + 1] - om[i]);
 
-    // grid-wide energy constants
-    const double u = fixed_unit(A.omega, A.n_omega, MODE, A.vtvg, A.fixed_bits);
-    const float fq = (float)(0.25 * A.vtvg / u);   // V_T/(4 V_G) in fixed-point units
-    const float om0 = A.omega[0];
-    const float omN = (MODE == TETRA_POINT) ? A.omega[A.n_omega - 1] : A.omega[A.n_omega];
-    const float inv_de =
-        (MODE == TETRA_POINT) ? (A.n_omega > 1 ? (float)(A.n_omega - 1) / (omN - om0) : 0.f)
-                              : (float)A.n_omega / (omN - om0);
-    float max_iw = 0.f;
-    if (MODE == TETRA_BIN) {
-        // every CTA needs the narrowest bin of the whole grid for the bound
-        for (int i = tid; i < A.n_omega; i += blockDim.x)
-            max_iw = fmaxf(max_iw, 1.0f / (A.omega[i + 1] - A.omega[i]));
-        for (int o = 16; o; o >>= 1) max_iw = fmaxf(max_iw, __shfl_xor_sync(0xffffffffu, max_iw, o));
-        if ((tid & 31) == 0) red_f[tid >> 5] = max_iw;
-        __syncthreads();
-        max_iw = 0.f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) max_iw = fmaxf(max_iw, red_f[i]);
-        __syncthreads();
+    // Work sequence of this CTA: item k -> (model, box). Single model: boxes
+    // blockIdx.x, blockIdx.x + gridDim.x, ...; batched: the contiguous global
+    // range [cta_begin[c], cta_begin[c+1]) of (model, box) in model order.
+    const int wbeg = (MAXM > 1) ? B.cta_begin[blockIdx.x] : 0;
+    const int wend = (MAXM > 1) ? B.cta_begin[blockIdx.x + 1] : 0;
+    auto work = [&](int k, int &mi, int &box) -> bool {
+        if (MAXM == 1) {
+            mi = 0;
+            box = blockIdx.x + k * gridDim.x;
+            return box < B.m[0].n_boxes;
+        }
+        const int g = wbeg + k;
+        if (g >= wend) return false;
+        int m = 0;
+        while (m + 1 < B.n_models && B.m[m + 1].box_base <= g) ++m;
+        mi = m;
+        box = g - B.m[m].box_base;
+        return true;
+    };
+    auto issue = [&](int k, int stg) {
+        int mi, box;
+        if (!work(k, mi, box)) return;
+        const ModelP &Mk = B.m[mi];
+        const int ix = box % Mk.nbx, iy = (box / Mk.nbx) % Mk.nby, iz = box / (Mk.nbx * Mk.nby);
+        mbar_arrive_expect_tx(&mbar[stg], A.e_box_bytes + A.w_box_bytes);
+        tma_load_4d(stage[stg], &B.maps[mi].e, 0, ix * A.BX, iy * A.BY, Mk.z0 + iz * A.BZ, &mbar[stg]);
+        tma_load_4d(stage[stg] + A.w_box_off, &B.maps[mi].w, 0, ix * A.BX, iy * A.BY,
+                    Mk.z0 + iz * A.BZ, &mbar[stg]);
+    };
+    __syncthreads();
+    // prologue: first two work items
+    if (tid == 0) {
+        issue(0, 0);
+        issue(1, 1);
     }
 
     const int PX = A.BX + 1, PY = A.BY + 1;
     const int ncube = A.BX * A.BY * A.BZ;   // a power of two
     const int lcube = A.lbx + A.lby + A.lbz;
-    long long *Gc = A.G + ((long)chunk * gridDim.x + blockIdx.x) * (long)A.n_orb * A.chunk_w;
 
-    // prologue: first two boxes
-    if (tid == 0) {
-        for (int k = 0; k < 2; ++k) {
-            const int box = blockIdx.x + k * gridDim.x;
-            if (box >= A.n_boxes) break;
-            const int ix = box % A.nbx, iy = (box / A.nbx) % A.nby, iz = box / (A.nbx * A.nby);
-            mbar_arrive_expect_tx(&mbar[k], A.e_box_bytes + A.w_box_bytes);
-            tma_load_4d(stage[k], &tm_eps, 0, ix * A.BX, iy * A.BY, A.z0 + iz * A.BZ, &mbar[k]);
-            tma_load_4d(stage[k] + A.w_box_off, &tm_w, 0, ix * A.BX, iy * A.BY,
-                        A.z0 + iz * A.BZ, &mbar[k]);
+    // state of the model whose boxes are being accumulated
+    int cur = -1, w0 = 0, wc = 0;
+    double u = 1.0;
+    float fq = 0.f, om0 = 0.f, inv_de = 0.f, max_iw = 0.f;
+    long long *Gc = A.G;
+    // moves the int32 tile of the current model into its int64 partial slot
+    auto flush_tile = [&]() {
+        for (int i = tid; i < A.n_orb * wc; i += blockDim.x) {
+            const int s = i / wc, j = i - s * wc;
+            const int v = tile[j * TS + s];
+            if (v)
+                atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j),
+                          static_cast<unsigned long long>(static_cast<long long>(v)));
         }
-    }
+    };
 
     for (int k = 0;; ++k) {
-        const int box = blockIdx.x + k * gridDim.x;
-        if (box >= A.n_boxes) break;
+        int mi, box;
+        if (!work(k, mi, box)) break;
+        const ModelP &M = B.m[mi];
+        if (mi != cur) {
+            // switch model: flush the previous one, reset the tile, cache the energy grid
+            if (cur >= 0) flush_tile();
+            __syncthreads();
+            cur = mi;
+            w0 = (MAXM == 1) ? chunk * A.chunk_w : 0;
+            wc = min(A.chunk_w, M.n_omega - w0);
+            const long slot = (MAXM == 1) ? (long)chunk * gridDim.x + blockIdx.x
+                                          : (long)M.pair_base + (blockIdx.x - M.c_lo);
+            Gc = A.G + slot * (long)A.n_orb * A.chunk_w;
+            for (int i = tid; i < TS * A.chunk_w; i += blockDim.x) tile[i] = 0;
+            for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
+            const int n_om = (MODE == TETRA_POINT) ? wc : wc + 1;
+            for (int i = tid; i < n_om; i += blockDim.x) om[i] = M.omega[w0 + i];
+            __syncthreads();
+            if (MODE == TETRA_BIN)
+                for (int i = tid; i < wc; i += blockDim.x) iw[i] = 1.0f / (om[i + 1] - om[i]);
+            u = fixed_unit(M.omega, M.n_omega, MODE, M.vtvg, M.fixed_bits);
+            fq = (float)(0.25 * M.vtvg / u);   // V_T/(4 V_G) in fixed-point units
+            om0 = M.omega[0];
+            const float omN = (MODE == TETRA_POINT) ? M.omega[M.n_omega - 1] : M.omega[M.n_omega];
+            inv_de = (MODE == TETRA_POINT) ? (M.n_omega > 1 ? (float)(M.n_omega - 1) / (omN - om0) : 0.f)
+                                           : (float)M.n_omega / (omN - om0);
+            if (MODE == TETRA_BIN) {
+                // the narrowest bin of the whole grid bounds every bin contribution
+                max_iw = 0.f;
+                for (int i = tid; i < M.n_omega; i += blockDim.x)
+                    max_iw = fmaxf(max_iw, 1.0f / (M.omega[i + 1] - M.omega[i]));
+                for (int o = 16; o; o >>= 1) max_iw = fmaxf(max_iw, __shfl_xor_sync(0xffffffffu, max_iw, o));
+                if ((tid & 31) == 0) red_f[tid >> 5] = max_iw;
+                __syncthreads();
+                max_iw = 0.f;
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) max_iw = fmaxf(max_iw, red_f[i]);
+            }
+            __syncthreads();
+        }
         const int st = k & 1;
         for (int i = tid; i < kKBins + 32 * A.n_classes; i += blockDim.x) (i < kKBins ? khist[i] : chist[i - kKBins]) = 0;
         const bool ok = mbar_wait_bounded(&mbar[st], (k >> 1) & 1, A.status);
@@ -405,8 +477,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const float *Es = reinterpret_cast<const float *>(stage[st]);
         const WT *Ws = reinterpret_cast<const WT *>(stage[st] + A.w_box_off);
-        const int ix = box % A.nbx, iy = (box / A.nbx) % A.nby, iz = box / (A.nbx * A.nby);
-        const int gx0 = ix * A.BX, gy0 = iy * A.BY, gz0 = A.z0 + iz * A.BZ;
+        const int ix = box % M.nbx, iy = (box / M.nbx) % M.nby, iz = box / (M.nbx * M.nby);
+        const int gx0 = ix * A.BX, gy0 = iy * A.BY, gz0 = M.z0 + iz * A.BZ;
 
         // Bmax = max |w| over the staged box (all of it, padding included, so it
         // bounds every orbital weight an item can read)
@@ -440,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int t = rest % 6, n = rest / 6;
             const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
             int K = 0, lo = 0;
-            if (gx0 + cx < A.n1 && gy0 + cy < A.n2 && gz0 + cz < A.z1) {
+            if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
                 float e1 = 3.0e38f, e4 = -3.0e38f;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -451,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     e4 = fmaxf(e4, ev);
                 }
                 int hi;
-                item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, A.n_omega, lo, hi);
+                item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, M.n_omega, lo, hi);
                 K = max(0, hi - lo + 1);
             }
             s_lo[it] = (short)(lo - w0);
@@ -562,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!(e[3] > e[0])) qmax = 3.0e38f;
             const bool fast = qmax < (float)A.fast_cap;
             const uint32_t gcube = (uint32_t)(gx0 + cx) +
-                                   (uint32_t)A.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)A.n2 * (uint32_t)(gz0 + cz));
+                                   (uint32_t)M.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)M.n2 * (uint32_t)(gz0 + cz));
             const float dith = item_dither((gcube * 6u + (uint32_t)t) * (uint32_t)A.nb + (uint32_t)n);
             if (fast) {
                 // every tile entry of these blocks may receive at most qmax from this item
@@ -621,17 +693,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncthreads();   // every thread is done reading stage[st] and adding to the tile
-        // refill this stage with box k+2
+        // refill this stage with work item k+2
         if (tid == 0) {
-            const int nbox = box + 2 * gridDim.x;
-            if (nbox < A.n_boxes) {
-                fence_proxy_async_smem();
-                const int jx = nbox % A.nbx, jy = (nbox / A.nbx) % A.nby, jz = nbox / (A.nbx * A.nby);
-                mbar_arrive_expect_tx(&mbar[st], A.e_box_bytes + A.w_box_bytes);
-                tma_load_4d(stage[st], &tm_eps, 0, jx * A.BX, jy * A.BY, A.z0 + jz * A.BZ, &mbar[st]);
-                tma_load_4d(stage[st] + A.w_box_off, &tm_w, 0, jx * A.BX, jy * A.BY,
-                            A.z0 + jz * A.BZ, &mbar[st]);
-            }
+            fence_proxy_async_smem();
+            issue(k + 2, st);
         }
         // A block whose bound reached kFlushAt is moved into the CTA's int64
         // partial before the next box: one box adds less than 2^30 - 2^20 to any
@@ -666,16 +731,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         return;
     }
-    for (int i = tid; i < A.n_orb * wc; i += blockDim.x) {
-        const int s = i / wc, j = i - s * wc;
-        const int v = tile[j * TS + s];
-        if (v)
-            atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j),
-                      static_cast<unsigned long long>(static_cast<long long>(v)));
-    }
+    if (cur >= 0) flush_tile();
 }
 
-// dos[s][w0+j] = u * sum over CTAs of the int64 partials (exact integer sum).
+// Single model: dos[s][w0+j] = u * sum over CTAs of the int64 partials (exact).
 __global__ void tetra_dos_reduce_kernel(const long long *G, int grid_x, int n_orb, int n_omega,
                                         int chunk_w, int mode, const float *omega, double vtvg,
                                         int bits, float *dos) {
@@ -692,37 +751,110 @@ __global__ void tetra_dos_reduce_kernel(const long long *G, int grid_x, int n_or
     }
 }
 
-template <int NORB, typename WT, int MODE>
-cudaError_t launch_t(const Plan &P, const CUtensorMap &te, const CUtensorMap &tw, const FwdArgs &A,
-                     cudaStream_t stream) {
-    auto k = tetra_dos_fwd_kernel<NORB, WT, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)P.smem_bytes);
-    if (e != cudaSuccess) return e;
-    dim3 grid(P.grid_x, P.n_chunks);
-    k<<<grid, kThreads, P.smem_bytes, stream>>>(te, tw, A);
-    return cudaGetLastError();
-}
-
-template <int NORB, int MODE>
-cudaError_t launch_wt(const Plan &P, const CUtensorMap &te, const CUtensorMap &tw,
-                      const FwdArgs &A, cudaStream_t stream) {
-    switch (P.d.weight_dtype) {
-        case TETRA_F16: return launch_t<NORB, __half, MODE>(P, te, tw, A, stream);
-        case TETRA_BF16: return launch_t<NORB, __nv_bfloat16, MODE>(P, te, tw, A, stream);
-        default: return launch_t<NORB, float, MODE>(P, te, tw, A, stream);
+// Batched: model blockIdx.y sums its partial slots [pair_base, pair_base + n_pairs).
+struct BatchOut {
+    float *dos[kMaxBatch];
+    int n_pairs[kMaxBatch];
+};
+__global__ void tetra_dos_reduce_batched(const __grid_constant__ Batch<kMaxBatch> B, const BatchOut O,
+                                         const long long *G, int n_orb, int chunk_w, int mode) {
+    const ModelP &M = B.m[blockIdx.y];
+    const double u = fixed_unit(M.omega, M.n_omega, mode, M.vtvg, M.fixed_bits);
+    const long total = (long)n_orb * M.n_omega;
+    const int np = O.n_pairs[blockIdx.y];
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / M.n_omega), i = (int)(idx - (long)s * M.n_omega);
+        const long long *g = G + ((long)M.pair_base * n_orb + s) * chunk_w + i;
+        long long acc = 0;
+        for (int c = 0; c < np; ++c) acc += g[(long)c * n_orb * chunk_w];
+        O.dos[blockIdx.y][idx] = (float)((double)acc * u);
     }
 }
 
-template <int MODE>
-cudaError_t launch_norb(const Plan &P, const CUtensorMap &te, const CUtensorMap &tw,
+template <int NORB, typename WT, int MODE, int MAXM>
+cudaError_t launch_t(size_t smem, dim3 grid, const Batch<MAXM> &Bt, const FwdArgs &A,
+                     cudaStream_t stream) {
+    auto k = tetra_dos_fwd_kernel<NORB, WT, MODE, MAXM>;
+    // The shared-memory opt-in is set once per device and size, so that a
+    // launch inside a CUDA-graph capture makes no attribute call.
+    static std::atomic<int> opted[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || opted[dev].load() < (int)smem) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) {
+            int cur = opted[dev].load();
+            while (cur < (int)smem && !opted[dev].compare_exchange_weak(cur, (int)smem)) {
+            }
+        }
+    }
+    k<<<grid, kThreads, smem, stream>>>(Bt, A);
+    return cudaGetLastError();
+}
+
+template <int NORB, int MODE, int MAXM>
+cudaError_t launch_wt(int wdtype, size_t smem, dim3 grid, const Batch<MAXM> &Bt, const FwdArgs &A,
+                      cudaStream_t stream) {
+    switch (wdtype) {
+        case TETRA_F16: return launch_t<NORB, __half, MODE, MAXM>(smem, grid, Bt, A, stream);
+        case TETRA_BF16: return launch_t<NORB, __nv_bfloat16, MODE, MAXM>(smem, grid, Bt, A, stream);
+        default: return launch_t<NORB, float, MODE, MAXM>(smem, grid, Bt, A, stream);
+    }
+}
+
+template <int MODE, int MAXM>
+cudaError_t launch_norb(int n_orb, int wdtype, size_t smem, dim3 grid, const Batch<MAXM> &Bt,
                         const FwdArgs &A, cudaStream_t stream) {
-    const int no = P.d.n_orb;
-    if (no <= 1) return launch_wt<1, MODE>(P, te, tw, A, stream);
-    if (no <= 2) return launch_wt<2, MODE>(P, te, tw, A, stream);
-    if (no <= 4) return launch_wt<4, MODE>(P, te, tw, A, stream);
-    if (no <= 8) return launch_wt<8, MODE>(P, te, tw, A, stream);
-    return launch_wt<16, MODE>(P, te, tw, A, stream);
+    if (n_orb <= 1) return launch_wt<1, MODE, MAXM>(wdtype, smem, grid, Bt, A, stream);
+    if (n_orb <= 2) return launch_wt<2, MODE, MAXM>(wdtype, smem, grid, Bt, A, stream);
+    if (n_orb <= 4) return launch_wt<4, MODE, MAXM>(wdtype, smem, grid, Bt, A, stream);
+    if (n_orb <= 8) return launch_wt<8, MODE, MAXM>(wdtype, smem, grid, Bt, A, stream);
+    return launch_wt<16, MODE, MAXM>(wdtype, smem, grid, Bt, A, stream);
+}
+
+// Launch constants shared by all models of a plan (box geometry, strides).
+void fill_common(const Plan &P, FwdArgs &A) {
+    A.nb = P.d.n_bands; A.n_orb = P.d.n_orb;
+    A.BX = P.BX; A.BY = P.BY; A.BZ = P.BZ;
+    A.lbx = __builtin_ctz(P.BX); A.lby = __builtin_ctz(P.BY); A.lbz = __builtin_ctz(P.BZ);
+    A.n_classes = (P.items_per_box + 95) / 96;
+    A.eps_stride = P.eps_stride; A.w_stride = P.w_stride;
+    const uint32_t npts = (uint32_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
+    A.e_box_bytes = npts * P.eps_stride * 4u;
+    A.w_box_bytes = npts * P.w_stride * (uint32_t)P.wbytes;
+    // every TMA destination starts on a 128-byte boundary
+    A.w_box_off = (A.e_box_bytes + 127u) & ~127u;
+    A.stage_bytes = (A.w_box_off + A.w_box_bytes + 127u) & ~127u;
+    A.chunk_w = P.chunk_w;
+    A.items_per_box = P.items_per_box;
+    long cap = ((1L << 30) - (1L << 20)) / A.items_per_box;
+    if (cap > (1L << 21)) cap = 1L << 21;
+    A.fast_cap = (int)cap;
+}
+
+ModelP model_of(const Plan &P, const float *omega) {
+    ModelP m;
+    m.n1 = P.d.n1; m.n2 = P.d.n2; m.n3 = P.d.n3; m.z0 = P.z0; m.z1 = P.z1;
+    m.nbx = P.nbx; m.nby = P.nby; m.n_boxes = P.n_boxes; m.n_omega = P.d.n_omega;
+    m.fixed_bits = P.fixed_bits;
+    m.box_base = 0; m.pair_base = 0; m.c_lo = 0;
+    m.vtvg = 1.0 / (6.0 * (double)P.d.n1 * (double)P.d.n2 * (double)P.d.n3);
+    m.omega = omega;
+    return m;
+}
+
+tetra_status_t encode_maps(const Plan &P, const float *eps, const void *w, MapPair &mp) {
+    const CUtensorMapDataType wdt = P.d.weight_dtype == TETRA_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                    : P.d.weight_dtype == TETRA_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    tetra_status_t st = encode_point_map(&mp.e, eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.eps_stride,
+                                         P.nx, P.ny, P.nz, P.BX + 1, P.BY + 1, P.BZ + 1);
+    if (st != TETRA_OK) return st;
+    return encode_point_map(&mp.w, w, wdt, P.wbytes, P.w_stride, P.nx, P.ny, P.nz, P.BX + 1,
+                            P.BY + 1, P.BZ + 1);
 }
 
 }  // namespace
@@ -741,52 +873,78 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
                                   cudaStream_t stream) {
     const size_t need = dos_forward_workspace(P);
     if (ws_bytes < need) return TETRA_ENOMEM;
-    CUtensorMap te, tw;
-    const CUtensorMapDataType wdt = P.d.weight_dtype == TETRA_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                    : P.d.weight_dtype == TETRA_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    tetra_status_t st = encode_point_map(&te, eps, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.eps_stride,
-                                         P.nx, P.ny, P.nz, P.BX + 1, P.BY + 1, P.BZ + 1);
+    static thread_local Batch<1> Bt;   // 0.3 KB of tensor maps + model constants
+    Bt.n_models = 1;
+    Bt.cta_begin[0] = 0;
+    tetra_status_t st = encode_maps(P, eps, w, Bt.maps[0]);
     if (st != TETRA_OK) return st;
-    st = encode_point_map(&tw, w, wdt, P.wbytes, P.w_stride, P.nx, P.ny, P.nz, P.BX + 1, P.BY + 1,
-                          P.BZ + 1);
-    if (st != TETRA_OK) return st;
+    Bt.m[0] = model_of(P, omega);
     FwdArgs A;
-    A.n1 = P.d.n1; A.n2 = P.d.n2; A.n3 = P.d.n3; A.nb = P.d.n_bands; A.n_orb = P.d.n_orb;
-    A.n_omega = P.d.n_omega;
-    A.z0 = P.z0; A.z1 = P.z1;
-    A.BX = P.BX; A.BY = P.BY; A.BZ = P.BZ; A.nbx = P.nbx; A.nby = P.nby; A.n_boxes = P.n_boxes;
-    A.lbx = __builtin_ctz(P.BX); A.lby = __builtin_ctz(P.BY); A.lbz = __builtin_ctz(P.BZ);
-    A.n_classes = (P.items_per_box + 95) / 96;
-    A.eps_stride = P.eps_stride; A.w_stride = P.w_stride;
-    const uint32_t npts = (uint32_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
-    A.e_box_bytes = npts * P.eps_stride * 4u;
-    A.w_box_bytes = npts * P.w_stride * (uint32_t)P.wbytes;
-    // every TMA destination starts on a 128-byte boundary
-    A.w_box_off = (A.e_box_bytes + 127u) & ~127u;
-    A.stage_bytes = (A.w_box_off + A.w_box_bytes + 127u) & ~127u;
-    A.chunk_w = P.chunk_w;
-    A.items_per_box = P.items_per_box;
-    long cap = ((1L << 30) - (1L << 20)) / A.items_per_box;
-    if (cap > (1L << 21)) cap = 1L << 21;
-    A.fast_cap = (int)cap;
-    A.fixed_bits = P.fixed_bits;
-    A.vtvg = 1.0 / (6.0 * (double)P.d.n1 * (double)P.d.n2 * (double)P.d.n3);
-    A.omega = omega;
-    int *status = reinterpret_cast<int *>(ws);
-    A.status = status;
+    fill_common(P, A);
+    A.status = reinterpret_cast<int *>(ws);
     A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
     cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);
     if (e != cudaSuccess) return TETRA_ECUDA;
-    e = (P.d.mode == TETRA_POINT) ? launch_norb<TETRA_POINT>(P, te, tw, A, stream)
-                                  : launch_norb<TETRA_BIN>(P, te, tw, A, stream);
+    const dim3 grid(P.grid_x, P.n_chunks);
+    e = (P.d.mode == TETRA_POINT)
+            ? launch_norb<TETRA_POINT, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt, A, stream)
+            : launch_norb<TETRA_BIN, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt, A, stream);
     if (e != cudaSuccess) return TETRA_ECUDA;
     const long total = (long)P.d.n_orb * P.d.n_omega;
     const int rb = 256;
     const int rg = (int)std::min<long>((total + rb - 1) / rb, 4L * P.sm_count);
     tetra_dos_reduce_kernel<<<rg, rb, 0, stream>>>(A.G, P.grid_x, P.d.n_orb, P.d.n_omega,
-                                                   P.chunk_w, P.d.mode, omega, A.vtvg,
+                                                   P.chunk_w, P.d.mode, omega, Bt.m[0].vtvg,
                                                    P.fixed_bits, dos);
+    if (cudaGetLastError() != cudaSuccess) return TETRA_ECUDA;
+    return TETRA_OK;
+}
+
+size_t dos_batched_workspace(const BatchPlan &B) {
+    return kStatusBytes + sizeof(long long) * (size_t)B.n_slots * B.models[0].d.n_orb * (size_t)B.chunk_w;
+}
+
+tetra_status_t launch_dos_batched(const BatchPlan &BP, const float *const *eps, const void *const *w,
+                                  const float *const *omega, float *const *dos, void *ws,
+                                  size_t ws_bytes, cudaStream_t stream) {
+    const size_t need = dos_batched_workspace(BP);
+    if (ws_bytes < need) return TETRA_ENOMEM;
+    std::unique_ptr<Batch<kMaxBatch>> Bt(new (std::nothrow) Batch<kMaxBatch>());
+    std::unique_ptr<BatchOut> O(new (std::nothrow) BatchOut());
+    if (!Bt || !O) return TETRA_ENOMEM;
+    Bt->n_models = BP.n_models;
+    for (int m = 0; m < BP.n_models; ++m) {
+        const Plan &P = BP.models[m];
+        tetra_status_t st = encode_maps(P, eps[m], w[m], Bt->maps[m]);
+        if (st != TETRA_OK) return st;
+        ModelP mp = model_of(P, omega[m]);
+        mp.box_base = BP.box_base[m];
+        mp.pair_base = BP.pair_base[m];
+        mp.c_lo = BP.c_lo[m];
+        Bt->m[m] = mp;
+        O->dos[m] = dos[m];
+        O->n_pairs[m] = BP.n_pairs[m];
+    }
+    for (int c = 0; c <= BP.grid_x; ++c) Bt->cta_begin[c] = BP.cta_begin[c];
+    const Plan &P0 = BP.models[BP.big];
+    FwdArgs A;
+    fill_common(P0, A);
+    A.chunk_w = BP.chunk_w;
+    A.status = reinterpret_cast<int *>(ws);
+    A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
+    cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);
+    if (e != cudaSuccess) return TETRA_ECUDA;
+    const dim3 grid(BP.grid_x, 1);
+    const int n_orb = P0.d.n_orb, wdt = P0.d.weight_dtype;
+    e = (P0.d.mode == TETRA_POINT)
+            ? launch_norb<TETRA_POINT, kMaxBatch>(n_orb, wdt, BP.smem_bytes, grid, *Bt, A, stream)
+            : launch_norb<TETRA_BIN, kMaxBatch>(n_orb, wdt, BP.smem_bytes, grid, *Bt, A, stream);
+    if (e != cudaSuccess) return TETRA_ECUDA;
+    const long total = (long)n_orb * BP.chunk_w;
+    const int rb = 256;
+    const int rg = (int)std::max<long>(1, std::min<long>((total + rb - 1) / rb, 64));
+    tetra_dos_reduce_batched<<<dim3(rg, BP.n_models), rb, 0, stream>>>(*Bt, *O, A.G, n_orb,
+                                                                        BP.chunk_w, P0.d.mode);
     if (cudaGetLastError() != cudaSuccess) return TETRA_ECUDA;
     return TETRA_OK;
 }

@@ -110,6 +110,10 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
     const WT *W = static_cast<const WT *>(A.w);
     float *ge = A.geps + p * A.eps_stride + n;
     float *gw = A.gw + p * A.w_stride + (long)n * A.n_orb;
+    if (n == 0) {   // the point's padding entries are written too (zeros)
+        for (int i = A.nb; i < A.eps_stride; ++i) A.geps[p * A.eps_stride + i] = 0.f;
+        for (int i = A.nb * A.n_orb; i < A.w_stride; ++i) A.gw[p * A.w_stride + i] = 0.f;
+    }
     if (px >= A.n1 || py >= A.n2 || pz >= A.n3) {   // halo copy: no own gradient
         *ge = 0.f;
         for (int s = 0; s < A.n_orb; ++s) gw[s] = 0.f;

@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
     for (int i = threadIdx.x; i < 3 * A.n_R; i += blockDim.x) s_R[i] = A.R[i];
     __syncthreads();
     const long P = (long)A.nx * A.ny * A.nz;
-    const long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (p >= P) return;
+    const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const long p = q + (long)A.z_off * A.nx * A.ny;   // padded point index
     const int px = (int)(p % A.nx), py = (int)((p / A.nx) % A.ny), pz = (int)(p / ((long)A.nx * A.ny));
     const int x = px % A.n1, y = py % A.n2, z = pz % A.n3;
 
@@ -90,7 +91,10 @@ tetra_status_t launch_eig(const Plan &P, const tetra_model_t *m, float *eps, voi
     if (m->n_R < 0 || m->n_R > kMaxR) return TETRA_EINVAL;
     EigArgs A;
     A.n1 = P.d.n1; A.n2 = P.d.n2; A.n3 = P.d.n3;
-    A.nx = P.nx; A.ny = P.ny; A.nz = P.nz;
+    A.nx = P.nx; A.ny = P.ny;
+    // a slab plan needs the points of its cube planes z0 .. z1 (upper halo included)
+    A.z_off = P.z0;
+    A.nz = P.z1 - P.z0 + 1;
     A.n_R = m->n_R;
     A.eps_stride = P.eps_stride; A.w_stride = P.w_stride; A.n_orb_out = P.d.n_orb;
     A.params = m->params; A.R = m->R; A.eps = eps; A.w = w;

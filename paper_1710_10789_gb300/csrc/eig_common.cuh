@@ -10,7 +10,8 @@ constexpr int kEigThreads = 128;
 constexpr int kMaxR = 32;
 
 struct EigArgs {
-    int n1, n2, n3, nx, ny, nz;
+    int n1, n2, n3, nx, ny;
+    int z_off, nz;   // padded planes z_off .. z_off + nz - 1 are computed
     int n_R;
     int eps_stride, w_stride, n_orb_out;
     const float *params;

@@ -30,6 +30,29 @@ struct tetra_plan_s {
     size_t smem_bytes;
 };
 
+// Host-side plan of a batch of independent models evaluated by one launch of
+// the forward kernel: per-model plans with a common box shape, and the static
+// schedule of (model, box) work over the persistent CTAs.
+namespace tetra {
+constexpr int kMaxBatch = 64;
+constexpr int kMaxBatchCtas = 1024;
+}  // namespace tetra
+struct tetra_batch_plan_s {
+    int n_models;
+    int device;
+    tetra_plan_s models[tetra::kMaxBatch];   // common box shape, one energy chunk each
+    int big;                          // model with the most energies
+    int chunk_w;                      // energies per shared tile (= max n_omega)
+    size_t smem_bytes;
+    int grid_x;                       // persistent CTAs
+    int n_slots;                      // int64 partial-sum slots
+    int box_base[tetra::kMaxBatch];          // first global work index of each model
+    int pair_base[tetra::kMaxBatch];         // first partial slot of each model
+    int c_lo[tetra::kMaxBatch];              // first CTA holding boxes of each model
+    int n_pairs[tetra::kMaxBatch];           // CTAs holding boxes of each model
+    int cta_begin[tetra::kMaxBatchCtas + 1]; // CTA c takes global work [cta_begin[c], cta_begin[c+1])
+};
+
 namespace tetra {
 
 // ---------------------------------------------------------------- status flags
@@ -149,6 +172,13 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
                                   const float *omega, float *dos, void *ws, size_t ws_bytes,
                                   cudaStream_t stream);
 size_t dos_forward_workspace(const Plan &P);
+using BatchPlan = ::tetra_batch_plan_s;
+tetra_status_t launch_dos_batched(const BatchPlan &B, const float *const *eps, const void *const *w,
+                                  const float *const *omega, float *const *dos, void *ws,
+                                  size_t ws_bytes, cudaStream_t stream);
+size_t dos_batched_workspace(const BatchPlan &B);
+tetra_status_t plan_init(Plan &P, const tetra_desc_t &d, int device, const int box[3], int ctas_per_sm);
+void default_box(const tetra_desc_t &d, int box[3]);
 tetra_status_t launch_dos_backward(const Plan &P, const float *eps, const void *w,
                                    const float *omega, const float *grad_dos, float *grad_eps,
                                    float *grad_w, void *ws, size_t ws_bytes, cudaStream_t stream);

@@ -65,3 +65,18 @@ def test_null_arguments_are_rejected(built):
     assert built.tetra_eig(None, None, None, None, None) == T.TETRA_EINVAL
     assert built.tetra_workspace_bytes(None) == 0
     assert built.tetra_plan_destroy(None) == T.TETRA_OK
+
+
+def test_batched_plan_rejects_bad_batches(built):
+    good = T.TetraDesc(8, 8, 8, 8, 8, 100, 0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    for descs in ([], [good] * (T.TETRA_MAX_BATCH + 1),
+                  [good, T.TetraDesc(8, 8, 8, 4, 8, 100, 0, 0, 0, 0)],     # n_bands differ
+                  [good, T.TetraDesc(8, 8, 8, 8, 4, 100, 0, 0, 0, 0)],     # n_orb differ
+                  [good, T.TetraDesc(8, 8, 8, 8, 8, 100, 1, 0, 0, 0)],     # mode differs
+                  [good, T.TetraDesc(8, 8, 8, 8, 8, 100, 0, 1, 0, 0)]):    # dtype differs
+        arr = (T.TetraDesc * max(1, len(descs)))(*descs)
+        assert built.tetra_plan_batched(ctypes.byref(h), arr, len(descs), None, 0) == T.TETRA_EINVAL
+        assert h.value is None
+    assert built.tetra_batch_workspace_bytes(None) == 0
+    assert built.tetra_batch_plan_destroy(None) == T.TETRA_OK

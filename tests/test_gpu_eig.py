@@ -91,3 +91,23 @@ def test_64cube_sampled_points(T):
     ev = np.linalg.eigvalsh(Hs)
     e = E[pts[:, 2], pts[:, 1], pts[:, 0], :8]
     assert np.max(np.abs(e - ev)) < 5e-5
+
+
+def test_slab_plan_writes_only_its_planes(T):
+    """A slab plan (cube planes [2, 5)) computes the point planes 2..5, bit for
+    bit as the whole-grid plan does, and leaves every other plane untouched."""
+    n = (6, 5, 7)
+    model = tbgen.tb_model(33, n_orb=8)
+    _, E, W = gpu_eig(T, model, n)
+    plan = T.Plan(*n, 8, 8, 16, z_range=(2, 5))
+    p, R = model_arrays(model)
+    dev = torch.device("cuda")
+    eps, w = plan.empty_inputs()
+    eps.fill_(float("nan"))
+    w.fill_(float("nan"))
+    plan.eig(torch.from_numpy(p).to(dev), torch.from_numpy(R).to(dev), eps, w)
+    torch.cuda.synchronize()
+    Es, Ws = eps.cpu().numpy(), w.cpu().numpy()
+    assert np.array_equal(Es[2:6], E[2:6]) and np.array_equal(Ws[2:6], W[2:6])
+    assert np.isnan(Es[:2]).all() and np.isnan(Es[6:]).all()
+    assert np.isnan(Ws[:2]).all() and np.isnan(Ws[6:]).all()
