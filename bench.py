@@ -217,6 +217,46 @@ def precision_variants(torch, T, n, nw, mode, params, R, omega, dos32, steps, wa
     return out
 
 
+def differentiation_workload(torch, T, steps, warmup, local):
+    """Loss = sum (bin DOS - target)^2 on the 8-orbital model, 64^3 grid, 200
+    bins; one step = forward (eig + bin DOS) and backward through both
+    adjoints to the model parameters. Target from a second seeded model."""
+    import tbgen
+    from paper_1710_10789_gb300.autograd import model_dos
+    dev = torch.device("cuda", local)
+    n, nbins = 64, 200
+    plan = T.Plan(n, n, n, 8, 8, nbins, mode="bin", device=local)
+    pt, Rt = (torch.from_numpy(a).to(dev) for a in model_arrays(tbgen.tb_model(1, n_orb=8)))
+    et, wt = plan.eig(pt, Rt)
+    lo, hi = float(et[..., :8].min()) - 0.1, float(et[..., :8].max()) + 0.1
+    edges = torch.from_numpy(tbgen.bin_edges(lo, hi, nbins)).to(dev)
+    target = plan.dos(et, wt, edges).clone()
+    p0, R0 = (torch.from_numpy(a).to(dev) for a in model_arrays(tbgen.tb_model(0, n_orb=8)))
+    params = p0.clone().requires_grad_(True)
+
+    def step():
+        params.grad = None
+        loss = ((model_dos(params, R0, edges, plan) - target) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    s_ = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s_)
+    for _ in range(steps):
+        step()
+    b.record(s_)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"workload": "8-orbital model, 64^3 grid, 200 bins, loss = sum (bin DOS - target)^2, "
+                        "forward + backward to 904 model parameters (eig, bin DOS, both adjoints)",
+            "ms_per_step": ms, "grad_norm": float(params.grad.norm())}
+
+
 def batched_workload(torch, T, mode, steps, warmup, local, tune=None, count_window=True):
     """64 seeded 8-orbital models, cubic grids N ~ U{16..96}, 500-3000 energies
     over each model's own band window; eigen-data by tetra_eig; all DOS in one
@@ -439,6 +479,7 @@ def main():
             "roofline": alu_roofline(torch, dev, bt["triples"], bt["items"], bt["ms"])}
         del bt
         torch.cuda.empty_cache()
+        variants["differentiation"] = differentiation_workload(torch, T, args.steps, args.warmup, local)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(n, nw, seed=0, planes=1)

@@ -645,10 +645,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 TetP TP;
                 tetp_setup(TP, e[0], e[1], e[2], e[3], fq);
                 if (fast) {
-                    int *col = tile + (lo - w0) * TS;
-                    for (int i = lo; i <= hi; ++i, col += TS) {
+                    // The walk over the window starts at a lane-dependent offset
+                    // and wraps: lanes whose windows coincide then add to
+                    // different tile rows at each step instead of serialising on
+                    // the same addresses. The sum does not depend on the order.
+                    const int K = hi - lo + 1;
+                    int i = lo + lane % K;
+                    for (int j = 0; j < K; ++j) {
                         float d[4];
                         tetp_dw(TP, om[i - w0], d);
+                        int *col = tile + (i - w0) * TS;
 #pragma unroll
                         for (int s = 0; s < NORB; ++s) {
                             float acc = fmaf(b[0][s], d[0], dith);
@@ -657,6 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             acc = fmaf(b[3][s], d[3], acc);
                             atomicAdd(col + s, __float_as_int(acc + kMagic) - kMagicBits);
                         }
+                        i = (i == hi) ? lo : i + 1;
                     }
                 } else {
                     for (int i = lo; i <= hi; ++i) {
