@@ -188,13 +188,12 @@ size_t tetra_eig_workspace_bytes(tetra_plan_t plan, int n_R);
 
 /* ---------------------------------------------------------------- batches
  * Many independent DOS problems in ONE launch of the forward kernel (not in
- * the paper, which evaluates one model at a time; Secs. III-IV). Each model has its
- * own k-grid, energy grid and data; all share n_bands, n_orb, mode and
- * weight_dtype. The persistent CTAs take contiguous ranges of (model, box)
- * work of equal estimated cost; per-model results are summed from exact
- * integer partials, so each model's DOS equals what tetra_dos gives for it up
- * to the fixed-point rounding of its own plan (bit-identical when both use the
- * same box shape and fixed-point bits).
+ * the paper, which evaluates one model at a time; Secs. III-IV). Each model has
+ * its own k-grid, energy grid and data; all share n_bands, n_orb, mode and
+ * weight_dtype. The persistent CTAs claim (model, box) work items from a
+ * global counter, so uneven models keep every SM busy; each model's result is
+ * summed in exact integers, so it equals what tetra_dos gives for it bit for
+ * bit (same fixed-point bits), whatever the schedule.
  * Every argument of tetra_dos_batched travels in kernel parameters, so the
  * call can be captured in a CUDA graph and replayed with the same pointers. */
 #define TETRA_MAX_BATCH 64
@@ -207,8 +206,6 @@ typedef struct {
                                 and clipped to the smallest grid); default 4,4,2
                                 for 8 bands                                        */
     int ctas_per_sm;         /* persistent CTAs per SM, default 1                  */
-    float item_cost;         /* schedule cost of one item's fixed work, in units of
-                                one energy step; default 3                         */
 } tetra_tune_t;
 
 /* Plans a batch of n_models (1..TETRA_MAX_BATCH) descriptions (host array).
@@ -228,7 +225,7 @@ tetra_status_t tetra_batch_layout(tetra_batch_plan_t plan, int model, tetra_layo
 size_t tetra_batch_workspace_bytes(tetra_batch_plan_t plan);
 
 /* Chosen launch shape (host call): box[3] cubes per box side, grid = persistent
- * CTAs, n_slots = int64 partial tiles. Any output pointer may be NULL. */
+ * CTAs, n_slots = int64 accumulators (one per model). Any output may be NULL. */
 tetra_status_t tetra_batch_info(tetra_batch_plan_t plan, int *box, int *grid, int *n_slots);
 
 /* DOS of every model of the batch (Sec. II.C, Eqs. (8)-(9), as tetra_dos).

@@ -68,7 +68,7 @@ class TetraLayout(ctypes.Structure):
 
 class TetraTune(ctypes.Structure):
     _fields_ = [("box_x", ctypes.c_int), ("box_y", ctypes.c_int), ("box_z", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int), ("item_cost", ctypes.c_float)]
+                ("ctas_per_sm", ctypes.c_int)]
 
 
 class TetraModel(ctypes.Structure):
@@ -371,8 +371,7 @@ class BatchPlan:
         self.tune = tune
         t = None
         if tune is not None:
-            t = TetraTune(*[int(x) for x in tune.get("box", (0, 0, 0))], int(tune.get("ctas_per_sm", 0)),
-                          float(tune.get("item_cost", 0.0)))
+            t = TetraTune(*[int(x) for x in tune.get("box", (0, 0, 0))], int(tune.get("ctas_per_sm", 0)))
         with torch.cuda.device(dev):
             self.handle = tetra_plan_batched(self.descs, t, dev)
         self.layouts = [tetra_batch_layout(self.handle, m) for m in range(len(self.descs))]

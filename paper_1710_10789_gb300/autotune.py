@@ -4,9 +4,8 @@ The paper varies the number of energies and cubes handled per thread block
 by hand and keeps the fastest (Sec. IV.B); here the same search runs
 automatically. For one batch signature (the models' grids and energy counts,
 bands, orbitals, mode, weight type) and one GPU it times each candidate box
-shape of the forward kernel (and optionally the schedule's per-item cost
-weight) on the caller's own inputs, each as a replayed CUDA graph, and keeps
-the fastest. Results are cached as JSON, keyed by the signature and the GPU,
+shape of the forward kernel on the caller's own inputs, each as a replayed
+CUDA graph, and keeps the fastest. Results are cached as JSON, keyed by the signature and the GPU,
 so a later process with the same batch skips the search.
 
 The launch shape never changes the result: the DOS is summed in exact
@@ -25,7 +24,6 @@ from . import BatchPlan, TetraError, tetra_version
 # shapes that clip to one already timed are skipped.
 BOX_CANDIDATES = ((4, 4, 2), (4, 4, 1), (4, 2, 2), (2, 4, 2), (2, 2, 4), (8, 4, 1), (8, 2, 2),
                   (4, 4, 4), (2, 2, 2))
-ITEM_COSTS = (3.0,)
 
 
 def cache_path() -> str:
@@ -77,10 +75,9 @@ def save_cache(path: str, cache: dict) -> None:
         raise
 
 
-def candidates(boxes=BOX_CANDIDATES, item_costs=ITEM_COSTS):
+def candidates(boxes=BOX_CANDIDATES):
     for b in boxes:
-        for c in item_costs:
-            yield {"box": [int(x) for x in b], "item_cost": float(c)}
+        yield {"box": [int(x) for x in b]}
 
 
 def graph_time(plan: BatchPlan, eps, w, omega, reps: int = 3) -> float:
@@ -107,8 +104,8 @@ def tune_batched(grids, n_omegas, n_bands, n_orb, eps=None, w=None, omega=None, 
                  weight_dtype="f32", cands=None, reps: int = 3, use_cache: bool = True,
                  path: str | None = None, measure=None, gpu: dict | None = None,
                  version: str | None = None) -> dict:
-    """Best launch shape for a batch: {"box": [bx, by, bz], "item_cost": c,
-    "seconds": t, "timed": [...]} (from the cache when present).
+    """Best launch shape for a batch: {"box": [bx, by, bz], "seconds": t,
+    "timed": [...]} (from the cache when present).
 
     `measure(tune) -> seconds or None` times one candidate; by default it
     builds a BatchPlan with that tune and replays a captured launch over
@@ -130,9 +127,9 @@ def tune_batched(grids, n_omegas, n_bands, n_orb, eps=None, w=None, omega=None, 
         except TetraError:
             return None   # this shape does not fit the device
         eff = tuple(plan.box)
-        if (eff, tune["item_cost"]) in seen:
+        if eff in seen:
             return None
-        seen.add((eff, tune["item_cost"]))
+        seen.add(eff)
         return graph_time(plan, eps, w, omega, reps)
 
     measure = measure or default_measure
@@ -140,12 +137,11 @@ def tune_batched(grids, n_omegas, n_bands, n_orb, eps=None, w=None, omega=None, 
     for tune in (cands if cands is not None else candidates()):
         t = measure(tune)
         if t is not None:
-            timed.append({"box": list(tune["box"]), "item_cost": tune["item_cost"], "seconds": t})
+            timed.append({"box": list(tune["box"]), "seconds": t})
     if not timed:
         raise RuntimeError("no candidate launch shape could be timed")
     best = min(timed, key=lambda r: r["seconds"])
-    result = {"box": best["box"], "item_cost": best["item_cost"], "seconds": best["seconds"],
-              "timed": timed}
+    result = {"box": best["box"], "seconds": best["seconds"], "timed": timed}
     if use_cache:
         cache = load_cache(path)
         cache[h] = {"key": key, "tune": result}

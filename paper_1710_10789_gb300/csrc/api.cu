@@ -5,7 +5,6 @@
 #include <cstring>
 #include <mutex>
 #include <new>
-#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -264,7 +263,7 @@ tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *
             d.weight_dtype != d0.weight_dtype)
             return TETRA_EINVAL;
     }
-    tetra_tune_t t = {0, 0, 0, 0, 0.f};
+    tetra_tune_t t = {0, 0, 0, 0};
     if (tune) t = *tune;
     int box[3];
     tetra::default_box(d0, box);
@@ -282,7 +281,6 @@ tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *
     }
     for (int i = 0; i < 3; ++i) box[i] = tetra::pow2_floor(std::max(1, box[i]));
     const int ctas_per_sm = t.ctas_per_sm > 0 ? t.ctas_per_sm : 1;
-    const double item_cost = t.item_cost > 0.f ? (double)t.item_cost : 3.0;
     tetra_batch_plan_s *B = new (std::nothrow) tetra_batch_plan_s();
     if (!B) return TETRA_ENOMEM;
     auto fail = [&](tetra_status_t s) {
@@ -302,55 +300,16 @@ tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *
     if (Pb.n_chunks != 1) return fail(TETRA_EUNSUPPORTED);
     B->chunk_w = Pb.chunk_w;
     B->smem_bytes = Pb.smem_bytes;
-    // Static schedule. Estimated cost of a box of model m: its items, each with
-    // a fixed part (corner loads, sort, window, set-up; item_cost energy-steps)
-    // and its window, about 0.72 n_omega h energies for an energy grid that
-    // spans the bands (h = mean 1/n of the grid; measured on the tight-binding
-    // models). Contiguous ranges of (model, box) work of equal estimated cost
-    // go to the persistent CTAs in model order.
-    long total_boxes = 0;
-    std::vector<double> cost(n_models);
-    double total = 0.0;
+    // work items: every box of every model, models in order; the CTAs claim
+    // them at run time
+    long total = 0;
     for (int m = 0; m < n_models; ++m) {
-        const Plan &P = B->models[m];
-        const double h = (1.0 / P.d.n1 + 1.0 / P.d.n2 + 1.0 / P.d.n3) / 3.0;
-        cost[m] = (double)P.items_per_box * (item_cost + 0.72 * P.d.n_omega * h);
-        B->box_base[m] = (int)total_boxes;
-        total_boxes += P.n_boxes;
-        total += cost[m] * P.n_boxes;
-        if (total_boxes > (1L << 30)) return fail(TETRA_EUNSUPPORTED);
+        B->box_base[m] = (int)total;
+        total += B->models[m].n_boxes;
+        if (total > (1L << 30)) return fail(TETRA_EUNSUPPORTED);
     }
-    const int G = (int)std::max<long>(1, std::min<long>({total_boxes, (long)ctas_per_sm * Pb.sm_count,
-                                                         (long)tetra::kMaxBatchCtas}));
-    B->grid_x = G;
-    {
-        int c = 0;
-        double acc = 0.0;
-        long g = 0;
-        B->cta_begin[0] = 0;
-        for (int m = 0; m < n_models; ++m) {
-            for (int b = 0; b < B->models[m].n_boxes; ++b) {
-                acc += cost[m];
-                ++g;
-                while (c + 1 < G && acc >= total * (double)(c + 1) / G) B->cta_begin[++c] = (int)g;
-            }
-        }
-        while (c < G) B->cta_begin[++c] = (int)total_boxes;
-    }
-    // partial-sum slots: one per (model, CTA holding boxes of it)
-    int slots = 0;
-    for (int m = 0; m < n_models; ++m) {
-        const int first = B->box_base[m], last = first + B->models[m].n_boxes - 1;
-        int lo = 0;
-        while (B->cta_begin[lo + 1] <= first) ++lo;
-        int hi = lo;
-        while (B->cta_begin[hi + 1] <= last) ++hi;
-        B->c_lo[m] = lo;
-        B->n_pairs[m] = hi - lo + 1;
-        B->pair_base[m] = slots;
-        slots += hi - lo + 1;
-    }
-    B->n_slots = slots;
+    B->total_boxes = (int)total;
+    B->grid_x = (int)std::max<long>(1, std::min<long>(total, (long)ctas_per_sm * Pb.sm_count));
     *plan = B;
     return TETRA_OK;
 }
@@ -378,7 +337,7 @@ tetra_status_t tetra_batch_info(tetra_batch_plan_t plan, int *box, int *grid, in
         box[2] = plan->models[0].BZ;
     }
     if (grid) *grid = plan->grid_x;
-    if (n_slots) *n_slots = plan->n_slots;
+    if (n_slots) *n_slots = plan->n_models;
     return TETRA_OK;
 }
 

@@ -7,10 +7,11 @@
 //    box's (BX+1)(BY+1)(BZ+1) corner points of all bands (energies and orbital
 //    weights, tetra layout) copied into shared memory by two 4-D TMA loads,
 //    double buffered across boxes. One model: boxes blockIdx.x, blockIdx.x +
-//    gridDim.x, ... (blockIdx.y = energy chunk). A batch of models: a
-//    contiguous range of (model, box) work, cut by the host into ranges of
-//    equal estimated cost; when the model changes the CTA flushes its tile to
-//    the previous model's partial slot and reloads the energy grid.
+//    gridDim.x, ... (blockIdx.y = energy chunk). A batch of models: each CTA
+//    claims the next (model, box) item from a global counter (models in
+//    order), so the work stays balanced whatever the models' costs; when the
+//    model changes the CTA flushes its tile into that model's int64
+//    accumulator with integer atomics and reloads the energy grid.
 //  * One thread handles one (tetrahedron, band) item: it reads the four corner
 //    energies, sorts them with a 5-comparator network carrying the corner
 //    positions (Sec. II.C sorts E1 <= E2 <= E3 <= E4), reads the orbital
@@ -30,7 +31,7 @@
 //    processed items bounds every tile entry; the tile is flushed into the
 //    CTA's int64 partial in global memory before it could overflow.
 //  * tetra_dos_reduce sums the per-CTA int64 partials (exact) and scales by u;
-//    for a batch, each model sums the slots of the CTAs that held its boxes.
+//    for a batch, each model's accumulator is scaled.
 #include <atomic>
 #include <memory>
 #include <new>
@@ -66,6 +67,7 @@ struct FwdArgs {
     int fast_cap;
     long long *G;        // int64 partials, [slot][n_orb][chunk_w]
     int *status;
+    int *queue;          // batched: next unclaimed (model, box) work item
 };
 
 // Fixed-point unit, identical in every kernel that uses it.
@@ -302,8 +304,6 @@ struct ModelP {
     int n1, n2, n3, z0, z1, nbx, nby, n_boxes, n_omega;
     int fixed_bits;
     int box_base;    // first global work index of the model (batched launches)
-    int pair_base;   // first partial-sum slot of the model (batched launches)
-    int c_lo;        // first CTA whose work range holds boxes of the model (batched)
     double vtvg;
     const float *omega;
 };
@@ -318,7 +318,7 @@ struct Batch {
     MapPair maps[MAXM];
     ModelP m[MAXM];
     int n_models;
-    int cta_begin[MAXM > 1 ? kMaxBatchCtas + 1 : 1];   // batched: CTA c takes global work [cta_begin[c], cta_begin[c+1])
+    int total_work;   // batched: (model, box) items of the launch
 };
 
 template <int NORB, typename WT, int MODE, int MAXM>
@@ -373,25 +373,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     // Work sequence of this CTA: item k -> (model, box). Single model: boxes
-    // blockIdx.x, blockIdx.x + gridDim.x, ...; batched: the contiguous global
-    // range [cta_begin[c], cta_begin[c+1]) of (model, box) in model order.
-    const int wbeg = (MAXM > 1) ? B.cta_begin[blockIdx.x] : 0;
-    const int wend = (MAXM > 1) ? B.cta_begin[blockIdx.x + 1] : 0;
+    // blockIdx.x, blockIdx.x + gridDim.x, ... Batched: thread 0 claims the next
+    // global item (models in order, boxes within a model) from a counter when
+    // it issues the item's TMA loads, so every CTA stays busy until the batch
+    // is done; s_work holds the claimed items of steps k .. k+2.
+    __shared__ int s_work[4];
     auto work = [&](int k, int &mi, int &box) -> bool {
         if (MAXM == 1) {
             mi = 0;
             box = blockIdx.x + k * gridDim.x;
             return box < B.m[0].n_boxes;
         }
-        const int g = wbeg + k;
-        if (g >= wend) return false;
+        const int g = s_work[k & 3];
+        if (g < 0) return false;
         int m = 0;
         while (m + 1 < B.n_models && B.m[m + 1].box_base <= g) ++m;
         mi = m;
         box = g - B.m[m].box_base;
         return true;
     };
-    auto issue = [&](int k, int stg) {
+    auto issue = [&](int k, int stg) {   // thread 0 only
+        if (MAXM > 1) {
+            const int g = atomicAdd(A.queue, 1);
+            s_work[k & 3] = g < B.total_work ? g : -1;
+        }
         int mi, box;
         if (!work(k, mi, box)) return;
         const ModelP &Mk = B.m[mi];
@@ -407,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         issue(0, 0);
         issue(1, 1);
     }
+    __syncthreads();
 
     const int PX = A.BX + 1, PY = A.BY + 1;
     const int ncube = A.BX * A.BY * A.BZ;   // a power of two
@@ -439,8 +445,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             cur = mi;
             w0 = (MAXM == 1) ? chunk * A.chunk_w : 0;
             wc = min(A.chunk_w, M.n_omega - w0);
-            const long slot = (MAXM == 1) ? (long)chunk * gridDim.x + blockIdx.x
-                                          : (long)M.pair_base + (blockIdx.x - M.c_lo);
+            // partial slot: one per (energy chunk, CTA) for a single model, one
+            // per model for a batch (CTAs flush into it with integer atomics)
+            const long slot = (MAXM == 1) ? (long)chunk * gridDim.x + blockIdx.x : (long)mi;
             Gc = A.G + slot * (long)A.n_orb * A.chunk_w;
             for (int i = tid; i < TS * A.chunk_w; i += blockDim.x) tile[i] = 0;
             for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
@@ -758,24 +765,20 @@ __global__ void tetra_dos_reduce_kernel(const long long *G, int grid_x, int n_or
     }
 }
 
-// Batched: model blockIdx.y sums its partial slots [pair_base, pair_base + n_pairs).
+// Batched: model blockIdx.y scales its int64 accumulator (slot = model).
 struct BatchOut {
     float *dos[kMaxBatch];
-    int n_pairs[kMaxBatch];
 };
 __global__ void tetra_dos_reduce_batched(const __grid_constant__ Batch<kMaxBatch> B, const BatchOut O,
                                          const long long *G, int n_orb, int chunk_w, int mode) {
     const ModelP &M = B.m[blockIdx.y];
     const double u = fixed_unit(M.omega, M.n_omega, mode, M.vtvg, M.fixed_bits);
     const long total = (long)n_orb * M.n_omega;
-    const int np = O.n_pairs[blockIdx.y];
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
          idx += (long)gridDim.x * blockDim.x) {
         const int s = (int)(idx / M.n_omega), i = (int)(idx - (long)s * M.n_omega);
-        const long long *g = G + ((long)M.pair_base * n_orb + s) * chunk_w + i;
-        long long acc = 0;
-        for (int c = 0; c < np; ++c) acc += g[(long)c * n_orb * chunk_w];
-        O.dos[blockIdx.y][idx] = (float)((double)acc * u);
+        const long long g = G[((long)blockIdx.y * n_orb + s) * chunk_w + i];
+        O.dos[blockIdx.y][idx] = (float)((double)g * u);
     }
 }
 
@@ -847,7 +850,7 @@ ModelP model_of(const Plan &P, const float *omega) {
     m.n1 = P.d.n1; m.n2 = P.d.n2; m.n3 = P.d.n3; m.z0 = P.z0; m.z1 = P.z1;
     m.nbx = P.nbx; m.nby = P.nby; m.n_boxes = P.n_boxes; m.n_omega = P.d.n_omega;
     m.fixed_bits = P.fixed_bits;
-    m.box_base = 0; m.pair_base = 0; m.c_lo = 0;
+    m.box_base = 0;
     m.vtvg = 1.0 / (6.0 * (double)P.d.n1 * (double)P.d.n2 * (double)P.d.n3);
     m.omega = omega;
     return m;
@@ -882,13 +885,14 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
     if (ws_bytes < need) return TETRA_ENOMEM;
     static thread_local Batch<1> Bt;   // 0.3 KB of tensor maps + model constants
     Bt.n_models = 1;
-    Bt.cta_begin[0] = 0;
+    Bt.total_work = P.n_boxes;
     tetra_status_t st = encode_maps(P, eps, w, Bt.maps[0]);
     if (st != TETRA_OK) return st;
     Bt.m[0] = model_of(P, omega);
     FwdArgs A;
     fill_common(P, A);
     A.status = reinterpret_cast<int *>(ws);
+    A.queue = nullptr;
     A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
     cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);
     if (e != cudaSuccess) return TETRA_ECUDA;
@@ -908,7 +912,7 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
 }
 
 size_t dos_batched_workspace(const BatchPlan &B) {
-    return kStatusBytes + sizeof(long long) * (size_t)B.n_slots * B.models[0].d.n_orb * (size_t)B.chunk_w;
+    return kStatusBytes + sizeof(long long) * (size_t)B.n_models * B.models[0].d.n_orb * (size_t)B.chunk_w;
 }
 
 tetra_status_t launch_dos_batched(const BatchPlan &BP, const float *const *eps, const void *const *w,
@@ -920,26 +924,24 @@ tetra_status_t launch_dos_batched(const BatchPlan &BP, const float *const *eps, 
     std::unique_ptr<BatchOut> O(new (std::nothrow) BatchOut());
     if (!Bt || !O) return TETRA_ENOMEM;
     Bt->n_models = BP.n_models;
+    Bt->total_work = BP.total_boxes;
     for (int m = 0; m < BP.n_models; ++m) {
         const Plan &P = BP.models[m];
         tetra_status_t st = encode_maps(P, eps[m], w[m], Bt->maps[m]);
         if (st != TETRA_OK) return st;
         ModelP mp = model_of(P, omega[m]);
         mp.box_base = BP.box_base[m];
-        mp.pair_base = BP.pair_base[m];
-        mp.c_lo = BP.c_lo[m];
         Bt->m[m] = mp;
         O->dos[m] = dos[m];
-        O->n_pairs[m] = BP.n_pairs[m];
     }
-    for (int c = 0; c <= BP.grid_x; ++c) Bt->cta_begin[c] = BP.cta_begin[c];
     const Plan &P0 = BP.models[BP.big];
     FwdArgs A;
     fill_common(P0, A);
     A.chunk_w = BP.chunk_w;
     A.status = reinterpret_cast<int *>(ws);
+    A.queue = reinterpret_cast<int *>(static_cast<unsigned char *>(ws) + kQueueOffset);
     A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
-    cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);
+    cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);   // status, counter, accumulators
     if (e != cudaSuccess) return TETRA_ECUDA;
     const dim3 grid(BP.grid_x, 1);
     const int n_orb = P0.d.n_orb, wdt = P0.d.weight_dtype;

@@ -23,7 +23,8 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
     __shared__ int s_R[3 * kMaxR];
     const int npar = N + 2 * A.n_R * N * N;
     for (int i = threadIdx.x; i < npar; i += blockDim.x) s_par[i] = A.params[i];
-    for (int i = threadIdx.x; i < 3 * A.n_R; i += blockDim.x) s_R[i] = A.R[i];
+    for (int i = threadIdx.x; i < 3 * A.n_R; i += blockDim.x)
+        s_R[i] = reduce_mod(A.R[i], i % 3 == 0 ? A.n1 : (i % 3 == 1 ? A.n2 : A.n3));
     __syncthreads();
     const long P = (long)A.nx * A.ny * A.nz;
     const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
     const int tid = threadIdx.x;
     const int npar = N + 2 * A.n_R * N * N;
     for (int i = tid; i < npar; i += blockDim.x) s_par[i] = A.params[i];
-    for (int i = tid; i < 3 * A.n_R; i += blockDim.x) s_R[i] = A.R[i];
+    for (int i = tid; i < 3 * A.n_R; i += blockDim.x)
+        s_R[i] = reduce_mod(A.R[i], i % 3 == 0 ? A.n1 : (i % 3 == 1 ? A.n2 : A.n3));
     __syncthreads();
     const long nk = (long)A.n1 * A.n2 * A.n3;
     // outputs owned by this thread: o = tid, tid + kBT, ... (accumulated in acc[o])

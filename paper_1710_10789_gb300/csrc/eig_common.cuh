@@ -41,28 +41,40 @@ __device__ __forceinline__ void hset(Mat<N> &M, int k, int p, float re, float im
 
 // Jacobi rotation zeroing H_pq (p < q): H <- U^H H U, V <- V U with
 // U_pp = c, U_pq = s, U_qp = -s e^{-i phi}, U_qq = c e^{-i phi}, H_pq = |h| e^{i phi}.
+struct Rot {
+    float c, s, er, ei;   // cos, sin, e^{-i phi}
+};
+
+// Parameters of the rotation for (p, q) from the current H; sets the new
+// H_pp, H_qq and zeroes H_pq. A coupling at the FP32 rounding level of ||H||
+// is dropped and the rotation becomes the identity (c = 1, s = 0, e = 1).
 template <int N, int p, int q>
-__device__ __forceinline__ bool rotate(Mat<N> &M) {
+__device__ __forceinline__ Rot rot_params(Mat<N> &M) {
     const float hr = M.hr[p][q], hi = M.hi[p][q];
-    const float h2 = hr * hr + hi * hi;
-    const float ha = sqrtf(h2);
+    const float ha = sqrtf(hr * hr + hi * hi);
     const float a = M.hr[p][p], b = M.hr[q][q];
-    // coupling at the FP32 rounding level of ||H||: drop it, no rotation
-    if (ha <= M.skip) {
-        M.hr[p][q] = 0.f;
-        M.hi[p][q] = 0.f;
-        return false;
-    }
-    const float ihs = 1.0f / ha;
-    const float er = hr * ihs, ei = -hi * ihs;   // e^{-i phi}
+    const bool act = ha > M.skip;
+    const float ihs = act ? 1.0f / ha : 0.f;
     const float tau = (b - a) * 0.5f * ihs;
-    const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-    const float c = rsqrtf(fmaf(t, t, 1.0f));
-    const float s = t * c;
+    const float tt = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+    const float t = act ? tt : 0.f;
+    const float c = act ? rsqrtf(fmaf(t, t, 1.0f)) : 1.f;
+    Rot R;
+    R.c = c;
+    R.s = t * c;
+    R.er = act ? hr * ihs : 1.f;
+    R.ei = act ? -hi * ihs : 0.f;
     M.hr[p][p] = a - t * ha;
     M.hr[q][q] = b + t * ha;
     M.hr[p][q] = 0.f;
     M.hi[p][q] = 0.f;
+    return R;
+}
+
+// Applies a rotation to the rest of H (rows/columns k != p, q) and to V.
+template <int N, int p, int q>
+__device__ __forceinline__ void rot_apply(Mat<N> &M, const Rot &R) {
+    const float c = R.c, s = R.s, er = R.er, ei = R.ei;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         if (k == p || k == q) continue;
@@ -81,17 +93,49 @@ __device__ __forceinline__ bool rotate(Mat<N> &M) {
         M.vr[i][p] = c * xr - s * zr; M.vi[i][p] = c * xi - s * zi;
         M.vr[i][q] = s * xr + c * zr; M.vi[i][q] = s * xi + c * zi;
     }
-    return true;
 }
 
-template <int N, int p, int q>
+// Round-robin (tournament) ordering of the N(N-1)/2 pairs: N' - 1 rounds of
+// N'/2 disjoint pairs (N' = N rounded up to even; pairs with the dummy index
+// N' - 1 >= N are left out). The rotations of one round touch disjoint
+// index pairs, so their parameters all come from the matrix at the start of
+// the round and can be computed independently (instruction-level
+// parallelism), then applied one after another.
+template <int N>
+struct RoundRobin {
+    static constexpr int M = (N + 1) & ~1;
+    __host__ __device__ static constexpr int a(int r, int i) { return i == 0 ? r : (r + i) % (M - 1); }
+    __host__ __device__ static constexpr int b(int r, int i) { return i == 0 ? M - 1 : (r - i + M - 1) % (M - 1); }
+    __host__ __device__ static constexpr int lo(int r, int i) { return a(r, i) < b(r, i) ? a(r, i) : b(r, i); }
+    __host__ __device__ static constexpr int hi(int r, int i) { return a(r, i) < b(r, i) ? b(r, i) : a(r, i); }
+};
+
+template <int N, int R, int I>
+struct RoundParams {
+    __device__ __forceinline__ static void run(Mat<N> &M, Rot *rot) {
+        constexpr int p = RoundRobin<N>::lo(R, I), q = RoundRobin<N>::hi(R, I);
+        if constexpr (q < N) rot[I] = rot_params<N, p, q>(M);
+        if constexpr (I + 1 < RoundRobin<N>::M / 2) RoundParams<N, R, I + 1>::run(M, rot);
+    }
+};
+
+template <int N, int R, int I>
+struct RoundApply {
+    __device__ __forceinline__ static void run(Mat<N> &M, const Rot *rot) {
+        constexpr int p = RoundRobin<N>::lo(R, I), q = RoundRobin<N>::hi(R, I);
+        if constexpr (q < N) rot_apply<N, p, q>(M, rot[I]);
+        if constexpr (I + 1 < RoundRobin<N>::M / 2) RoundApply<N, R, I + 1>::run(M, rot);
+    }
+};
+
+template <int N, int R>
 struct Sweep {
-    // one cyclic sweep over all pairs; returns whether any rotation was applied
-    __device__ __forceinline__ static bool run(Mat<N> &M) {
-        bool any = rotate<N, p, q>(M);
-        if constexpr (q + 1 < N) any |= Sweep<N, p, q + 1>::run(M);
-        else if constexpr (p + 2 < N) any |= Sweep<N, p + 1, p + 2>::run(M);
-        return any;
+    // rounds R .. N'-2 of one sweep
+    __device__ __forceinline__ static void run(Mat<N> &M) {
+        Rot rot[RoundRobin<N>::M / 2];
+        RoundParams<N, R, 0>::run(M, rot);
+        RoundApply<N, R, 0>::run(M, rot);
+        if constexpr (R + 2 < RoundRobin<N>::M) Sweep<N, R + 1>::run(M);
     }
 };
 
@@ -120,30 +164,38 @@ __device__ __forceinline__ void jacobi(Mat<N> &M) {
         // 1e-18 floor keeps |h|^2 out of the denormal range, where |h| (and with
         // it the phase h*/|h| of the rotation) would lose accuracy
         M.skip = 6e-8f * sqrtf(fro) + 1e-18f;
-        // cyclic sweeps until the squared off-diagonal norm is below 1e-14 of
+        // sweeps until the squared off-diagonal norm is below 1e-14 of
         // ||H||^2 (FP32 rounding level; convergence is quadratic), at most 12
         const float tol = 1e-14f * fro + 1e-30f;
         for (int sweep = 0; sweep < 12; ++sweep) {
             if (offdiag2(M) <= tol) break;
-            Sweep<N, 0, 1>::run(M);
+            Sweep<N, 0>::run(M);
         }
     }
 }
 
-// e^{i k.R} at grid point (x, y, z): 2 pi k.R reduced exactly with integer
-// arithmetic, m_i = (x_i R_i) mod n_i, before the single-precision sin/cos.
+// Lattice vector component reduced to [0, n): staged once per block so that
+// the phase needs only 32-bit products below n^2 <= 2^24.
+__device__ __forceinline__ int reduce_mod(int a, int n) {
+    const int m = a % n;
+    return m < 0 ? m + n : m;
+}
+
+// e^{i k.R} at grid point (x, y, z) for R given reduced mod (n1, n2, n3):
+// 2 pi k.R is reduced exactly with integer arithmetic, m_i = (x_i R_i) mod n_i,
+// before the single-precision sin/cos.
 __device__ __forceinline__ void phase(const int *R, int x, int y, int z, int n1, int n2, int n3,
                                       float &sn, float &cs) {
-    auto md = [](long a, int n) { long m = a % n; return m < 0 ? m + n : m; };
-    const long m0 = md((long)x * R[0], n1);
-    const long m1 = md((long)y * R[1], n2);
-    const long m2 = md((long)z * R[2], n3);
+    const int m0 = (x * R[0]) % n1;
+    const int m1 = (y * R[1]) % n2;
+    const int m2 = (z * R[2]) % n3;
     const float frac = (float)m0 / n1 + (float)m1 / n2 + (float)m2 / n3;
     sincospif(2.0f * frac, &sn, &cs);
 }
 
 // H(k) at grid point (x, y, z) from the model staged in shared memory
-// (s_par: onsite[N], Re t[n_R][N][N], Im t[n_R][N][N]; s_R: R[n_R][3]);
+// (s_par: onsite[N], Re t[n_R][N][N], Im t[n_R][N][N]; s_R: R[n_R][3] reduced
+// mod (n1, n2, n3));
 // upper triangle into M.
 template <int N>
 __device__ __forceinline__ void build_h(Mat<N> &M, const float *s_par, const int *s_R, int n_R,

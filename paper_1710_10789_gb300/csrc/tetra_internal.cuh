@@ -31,26 +31,21 @@ struct tetra_plan_s {
 };
 
 // Host-side plan of a batch of independent models evaluated by one launch of
-// the forward kernel: per-model plans with a common box shape, and the static
-// schedule of (model, box) work over the persistent CTAs.
+// the forward kernel: per-model plans with a common box shape. The persistent
+// CTAs take (model, box) work items from a global counter at run time.
 namespace tetra {
 constexpr int kMaxBatch = 64;
-constexpr int kMaxBatchCtas = 1024;
 }  // namespace tetra
 struct tetra_batch_plan_s {
     int n_models;
     int device;
     tetra_plan_s models[tetra::kMaxBatch];   // common box shape, one energy chunk each
-    int big;                          // model with the most energies
-    int chunk_w;                      // energies per shared tile (= max n_omega)
+    int big;                                 // model with the most energies
+    int chunk_w;                             // energies per shared tile (= max n_omega)
     size_t smem_bytes;
-    int grid_x;                       // persistent CTAs
-    int n_slots;                      // int64 partial-sum slots
+    int grid_x;                              // persistent CTAs
+    int total_boxes;                         // work items of the whole batch
     int box_base[tetra::kMaxBatch];          // first global work index of each model
-    int pair_base[tetra::kMaxBatch];         // first partial slot of each model
-    int c_lo[tetra::kMaxBatch];              // first CTA holding boxes of each model
-    int n_pairs[tetra::kMaxBatch];           // CTAs holding boxes of each model
-    int cta_begin[tetra::kMaxBatchCtas + 1]; // CTA c takes global work [cta_begin[c], cta_begin[c+1])
 };
 
 namespace tetra {
@@ -59,6 +54,7 @@ namespace tetra {
 // The first bytes of every workspace hold device-side status bits.
 enum : int { kFlagTimeout = 1, kFlagRange = 2, kFlagConfig = 4 };
 constexpr size_t kStatusBytes = 256;
+constexpr size_t kQueueOffset = 64;   // batched launches: work counter inside the status bytes
 
 using Plan = ::tetra_plan_s;
 
