@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *mbar = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(ccursor + 32 * A.n_classes) + 15) & ~uintptr_t(15));
     __shared__ float red_f[kThreads / 32];
-    __shared__ int s_abort, s_active;
+    __shared__ int s_abort, s_active, s_slot;
 
     // self-check of the shared-memory carve-up against the launch's dynamic size
     {
@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int st = k & 1;
         for (int i = tid; i < kKBins + 32 * A.n_classes; i += blockDim.x) (i < kKBins ? khist[i] : chist[i - kKBins]) = 0;
+        if (tid == 0) s_slot = 0;
         const bool ok = mbar_wait_bounded(&mbar[st], (k >> 1) & 1, A.status);
         if (__syncthreads_or(!ok)) {
             s_abort = 1;
@@ -603,8 +604,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         // finish together; it is residue-major, so the 32 lanes get windows that
         // start on (nearly) distinct tile rows mod 32 and their shared-memory
         // atomics hit distinct banks at every step.
+        // Warps claim the slots longest-window class first (a shared counter),
+        // which balances the warps' work before the end-of-box barrier.
         const int lane = tid & 31;
-        for (int slot = tid >> 5; slot < n_slots; slot += (int)(blockDim.x >> 5)) {
+        for (;;) {
+            int claim = 0;
+            if (lane == 0) claim = atomicAdd(&s_slot, 1);
+            claim = __shfl_sync(0xffffffffu, claim, 0);
+            if (claim >= n_slots) break;
+            const int slot = n_slots - 1 - claim;
             const int c = slot / 3;
             const int pos = c * kClassSize + (slot - 3 * c) + 3 * lane;
             if (pos >= n_active) continue;
