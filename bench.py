@@ -39,6 +39,13 @@ FP32_LANES_PER_SM = 128
 # triple with n_orb = 8, and per (tetra, band) item (sort, window, reciprocals)
 OPS_PER_TRIPLE = 44
 OPS_PER_ITEM = 40
+# DRAM bytes (read + write) of one tetra_dos_fwd_kernel launch from an ncu
+# capture of the 128^3, 4000-energy, FP32, point-mode launch, scaled by the
+# number of boxes to other cubic grids (the traffic is per box: halo reads of
+# the TMA boxes). Valid only for the kernel source it was taken from (first 16
+# hex digits of the SHA-256 of csrc/dos.cu); otherwise the bench reports null.
+DOS_TRAFFIC_CAPTURE = {"dos_cu_sha256": "4db8503c598a5dcb", "grid": 128, "n_omega": 4000,
+                       "bytes": 691787776 + 5411072}
 
 
 def parse():
@@ -157,6 +164,18 @@ def in_window_count(torch, eps, n, nb, omega, mode, zc=16):
                 hi = hi.clamp(max=om.numel() - 1)
             total += int((hi - lo).clamp(min=0).sum().item())
     return total
+
+
+def dos_traffic(n, n_omega, mode, weight_dtype):
+    """Captured DRAM bytes per forward launch scaled to an n^3 grid, or None
+    when the capture does not describe this kernel source or configuration."""
+    import hashlib
+    c = DOS_TRAFFIC_CAPTURE
+    src = os.path.join(ROOT, "paper_1710_10789_gb300", "csrc", "dos.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != c["dos_cu_sha256"] or n_omega != c["n_omega"] or mode != "point" or weight_dtype != "f32":
+        return None
+    return c["bytes"] * (n / c["grid"]) ** 3
 
 
 def alu_roofline(torch, dev, triples, items, ms):
@@ -458,6 +477,9 @@ def main():
     triples = in_window_count(torch, eps, n, 8, omega, args.mode)
     clocks = clk.summary()
     roof = alu_roofline(torch, dev, triples, n_tet * 8, dos_ms)
+    roof["traffic"] = dos_traffic(n, nw, args.mode, args.weight_dtype)
+    roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 launch "
+                              "scaled by boxes (see profiles/)")
     # end to end through the public API: host model in, host DOS out
     e2e = None
     if not args.quick:
