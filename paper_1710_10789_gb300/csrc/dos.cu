@@ -51,8 +51,20 @@ constexpr int kKBins = 256;     // window-length histogram bins (K >= 255 share 
 constexpr int kClassSize = 96;  // items per length class: 3 warps of 32
 
 // Table I, corner labels minus one; label c sits at offset (c&1, (c>>1)&1, (c>>2)&1).
-__constant__ int c_table[6][4] = {{0, 1, 2, 5}, {1, 2, 3, 5}, {0, 2, 4, 5},
-                                  {2, 3, 5, 7}, {2, 4, 5, 6}, {2, 5, 6, 7}};
+// Packed 3 bits per corner, 12 bits per tetrahedron, so that lanes holding
+// different tetrahedra decode their corners from an immediate instead of
+// serialising on divergent constant-memory reads.
+constexpr int kTableI[6][4] = {{0, 1, 2, 5}, {1, 2, 3, 5}, {0, 2, 4, 5},
+                               {2, 3, 5, 7}, {2, 4, 5, 6}, {2, 5, 6, 7}};
+constexpr uint32_t pack_tet(int t) {
+    return (uint32_t)(kTableI[t][0] | kTableI[t][1] << 3 | kTableI[t][2] << 6 | kTableI[t][3] << 9);
+}
+constexpr uint64_t kTetLo = (uint64_t)pack_tet(0) | (uint64_t)pack_tet(1) << 12 | (uint64_t)pack_tet(2) << 24 |
+                            (uint64_t)pack_tet(3) << 36 | (uint64_t)pack_tet(4) << 48;
+constexpr uint32_t kTetHi = pack_tet(5);
+__device__ __forceinline__ uint32_t tet_code(int t) {
+    return t < 5 ? (uint32_t)(kTetLo >> (12 * t)) & 0xFFFu : kTetHi;
+}
 
 // Launch constants shared by every model of a launch.
 struct FwdArgs {
@@ -352,6 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         (reinterpret_cast<uintptr_t>(ccursor + 32 * A.n_classes) + 15) & ~uintptr_t(15));
     __shared__ float red_f[kThreads / 32];
     __shared__ int s_abort, s_active, s_slot;
+    __shared__ int s_cdelta[8];   // staged-box point offset of cube corner c
 
     // self-check of the shared-memory carve-up against the launch's dynamic size
     {
@@ -365,6 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             return;
         }
     }
+    if (tid < 8)
+        s_cdelta[tid] = (tid & 1) + (A.BX + 1) * (((tid >> 1) & 1) + (A.BY + 1) * (tid >> 2));
     if (tid == 0) {
         s_abort = 0;
         mbar_init(&mbar[0], 1);
@@ -522,10 +537,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             int K = 0, lo = 0;
             if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
                 float e1 = 3.0e38f, e4 = -3.0e38f;
+                const uint32_t code = tet_code(t);
+                const int p0 = cx + PX * (cy + PY * cz);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int c = c_table[t][q];
-                    const int p = (cx + (c & 1)) + PX * ((cy + ((c >> 1) & 1)) + PY * (cz + ((c >> 2) & 1)));
+                    const int p = p0 + s_cdelta[(code >> (3 * q)) & 7];
                     const float ev = Es[p * A.eps_stride + n];
                     e1 = fminf(e1, ev);
                     e4 = fmaxf(e4, ev);
@@ -623,10 +639,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
             float e[4];
             int p[4];
+            const uint32_t code = tet_code(t);
+            const int p0 = cx + PX * (cy + PY * cz);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int c = c_table[t][q];
-                p[q] = (cx + (c & 1)) + PX * ((cy + ((c >> 1) & 1)) + PY * (cz + ((c >> 2) & 1)));
+                p[q] = p0 + s_cdelta[(code >> (3 * q)) & 7];
                 e[q] = Es[p[q] * A.eps_stride + n];
             }
             cswap(e[0], e[1], p[0], p[1]);
@@ -665,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // different tile rows at each step instead of serialising on
                     // the same addresses. The sum does not depend on the order.
                     const int K = hi - lo + 1;
-                    int i = lo + lane % K;
+                    int i = lo + ((lane * K) >> 5);
                     for (int j = 0; j < K; ++j) {
                         float d[4];
                         tetp_dw(TP, om[i - w0], d);
