@@ -92,11 +92,11 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     P.items_per_box = 6 * P.BX * P.BY * P.BZ * d.n_bands;
     if (P.items_per_box > 65535) return TETRA_EUNSUPPORTED;
     P.tile_stride = tetra::norb_template(d.n_orb) + 1;
-    // two TMA stages, per-item sort arrays, histogram, mbarriers, alignment
-    // slack and the kernel's static variables
-    const size_t n_classes = (P.items_per_box + 95) / 96;
-    const size_t fixed = 2 * stage + 7 * (size_t)P.items_per_box + 16 + (2 * 256 + 64 * n_classes) * 4 + 32 +
-                         1024 + 512 + 64;
+    // two TMA stages, per-item sort arrays, length histogram and cursors,
+    // mbarriers, alignment slack, the kernel's static variables and the tile's
+    // extra row
+    const size_t fixed = 2 * stage + 6 * (size_t)P.items_per_box + 16 + 2 * 256 * 4 + 32 + 1024 + 512 + 128 +
+                         4 * (size_t)P.tile_stride;
     // per energy: int tile row, cached energy, 1/width (bin mode), block bound share
     const size_t per_w = 4 * (size_t)(P.tile_stride + 1 + (d.mode == TETRA_BIN ? 1 : 0)) + 1;
     if (fixed + per_w * 64 > P.smem_optin) return TETRA_EUNSUPPORTED;
@@ -120,6 +120,9 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
         F = std::max(17, std::min(28, F));
         P.fixed_bits = env_int("TETRA_FIXED_BITS", F);
     }
+    // tile blocks are flushed at a bound of 2^30 (a lower value, for tests of
+    // the flush path, from TETRA_FLUSH_BITS)
+    P.flush_bits = std::max(8, std::min(30, env_int("TETRA_FLUSH_BITS", 30)));
     return TETRA_OK;
 }
 

@@ -17,14 +17,22 @@
 //    positions (Sec. II.C sorts E1 <= E2 <= E3 <= E4), reads the orbital
 //    weights in sorted order, and visits only the energies strictly inside
 //    (E1, E4) (bins overlapping it in bin mode); all others get zero weight.
+//  * Items of a box are ranked by window length (counting sort), so the 32
+//    lanes of a warp walk windows of nearly equal length.
 //  * Each visited energy adds sum_l b_{l,s} dw_l to the CTA's tile for every
 //    orbital s (Eq. (8)).
 //
 // Accumulation: exact fixed point, no float atomics anywhere
 //  * Contributions are scaled by 1/u, u = (V_T/V_G) / dE * 2^-F (dE = mean
 //    grid spacing, F = fixed_bits), rounded to integers and added with integer
-//    shared-memory atomics into an int32 tile [n_orb][energies]. Integer
+//    shared-memory atomics into an int32 tile [energies][n_orb + 1]. Integer
 //    addition is associative, so the tile does not depend on thread order.
+//  * The rounding adds 1.5 * 2^23 in FP32 and the tile receives the raw bit
+//    pattern, i.e. the integer plus the constant bias M = 0x4B400000. The
+//    extra column of each tile row counts (as differences: +1 at a window's
+//    first energy, -1 after its last) how many adds the row received, so a
+//    row's value is recovered modulo 2^32 as raw - count * M when it is
+//    flushed.
 //  * A per-item bound q_max (|b| <= Bmax of the box, and the tetrahedron DOS
 //    is at most 3/E41 of V_T/V_G) decides between this fast path and a 64-bit
 //    global integer path for rare near-flat tetrahedra. The sum of q_max over
@@ -44,11 +52,9 @@ namespace {
 
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float + kMagic rounds to an integer
 constexpr int kMagicBits = 0x4B400000;  // bit pattern of kMagic
-constexpr int kThreads = 512;
 constexpr uint32_t kSmemAlign = 1024;
-constexpr unsigned kFlushAt = 1u << 30;
+constexpr int kThreads = 512;
 constexpr int kKBins = 256;     // window-length histogram bins (K >= 255 share one)
-constexpr int kClassSize = 96;  // items per length class: 3 warps of 32
 
 // Table I, corner labels minus one; label c sits at offset (c&1, (c>>1)&1, (c>>2)&1).
 // Packed 3 bits per corner, 12 bits per tetrahedron, so that lanes holding
@@ -71,12 +77,12 @@ struct FwdArgs {
     int nb, n_orb;
     int BX, BY, BZ;
     int lbx, lby, lbz;   // log2 of the box sides (powers of two)
-    int n_classes;       // ceil(items_per_box / 96)
     int eps_stride, w_stride;
     uint32_t e_box_bytes, w_box_bytes, w_box_off, stage_bytes;   // w box at stage + w_box_off (128-aligned)
     int chunk_w;         // energies per shared tile (largest model of a batch)
-    int items_per_box;
+    int items_per_box;   // (tetrahedron, band) items per box
     int fast_cap;
+    unsigned flush_at;   // a 64-energy block is flushed once its bound reaches this
     long long *G;        // int64 partials, [slot][n_orb][chunk_w]
     int *status;
     int *queue;          // batched: next unclaimed (model, box) work item
@@ -99,6 +105,14 @@ __device__ __forceinline__ void cswap(float &ea, float &eb, int &pa, int &pb) {
     const float lo = s ? eb : ea, hi = s ? ea : eb;
     const int plo = s ? pb : pa, phi = s ? pa : pb;
     ea = lo; eb = hi; pa = plo; pb = phi;
+}
+
+__device__ __forceinline__ void sort4(float (&e)[4], int (&p)[4]) {
+    cswap(e[0], e[1], p[0], p[1]);
+    cswap(e[2], e[3], p[2], p[3]);
+    cswap(e[0], e[2], p[0], p[2]);
+    cswap(e[1], e[3], p[1], p[3]);
+    cswap(e[1], e[2], p[1], p[2]);
 }
 
 // Dither offset in [-1/2, 1/2) for one (tetrahedron, band) item, hashed from its
@@ -336,7 +350,10 @@ struct Batch {
 template <int NORB, typename WT, int MODE, int MAXM>
 __global__ void __launch_bounds__(kThreads, 1)
     tetra_dos_fwd_kernel(const __grid_constant__ Batch<MAXM> B, const FwdArgs A) {
-    constexpr int TS = NORB + 1;   // tile row: NORB orbitals + 1 pad (spreads banks)
+    // tile row: NORB orbitals + the row's add count (differences); the odd
+    // row length also spreads consecutive rows over the shared-memory banks
+    constexpr int TS = NORB + 1;
+    constexpr int CNT = NORB;
     extern __shared__ unsigned char smem_raw[];
     // TMA destinations need an aligned base; the dynamic area starts after the
     // static variables, so align it here (the host reserves kSmemAlign bytes).
@@ -346,23 +363,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int chunk = blockIdx.y;   // energy chunk (single-model launches)
     // shared memory carve-up
     unsigned char *stage[2] = {smem, smem + A.stage_bytes};
-    int *tile = reinterpret_cast<int *>(smem + 2 * A.stage_bytes);   // [chunk_w][TS]
-    float *om = reinterpret_cast<float *>(tile + TS * A.chunk_w);   // energies / edges
+    int *tile = reinterpret_cast<int *>(smem + 2 * A.stage_bytes);   // [chunk_w + 1][TS]
+    float *om = reinterpret_cast<float *>(tile + TS * (A.chunk_w + 1));   // energies / edges
     float *iw = om + A.chunk_w + 1;                                   // 1/bin width (bin mode)
     unsigned *blk_bound = reinterpret_cast<unsigned *>(iw + (MODE == TETRA_BIN ? A.chunk_w : 0));
     const int n_blk = (A.chunk_w + 63) >> 6;
     short *s_lo = reinterpret_cast<short *>(blk_bound + n_blk);      // window start - w0
     unsigned short *s_K = reinterpret_cast<unsigned short *>(s_lo + A.items_per_box);
     unsigned short *s_list = s_K + A.items_per_box;                 // items sorted by K
-    unsigned char *s_cls = reinterpret_cast<unsigned char *>(s_list + A.items_per_box);
     int *khist = reinterpret_cast<int *>(
-        (reinterpret_cast<uintptr_t>(s_cls + A.items_per_box) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(s_list + A.items_per_box) + 15) & ~uintptr_t(15));
     int *kcursor = khist + kKBins;           // rank cursors per window length
-    int *chist = kcursor + kKBins;           // (class, row residue) counters
-    int *ccursor = chist + 32 * A.n_classes; // scatter cursors per (class, residue)
     uint64_t *mbar = reinterpret_cast<uint64_t *>(
-        (reinterpret_cast<uintptr_t>(ccursor + 32 * A.n_classes) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(kcursor + kKBins) + 15) & ~uintptr_t(15));
     __shared__ float red_f[kThreads / 32];
+    __shared__ int s_wsum[kThreads / 32];
     __shared__ int s_abort, s_active, s_slot;
     __shared__ int s_cdelta[8];   // staged-box point offset of cube corner c
 
@@ -438,11 +453,68 @@ __global__ void __launch_bounds__(kThreads, 1)
     double u = 1.0;
     float fq = 0.f, om0 = 0.f, inv_de = 0.f, max_iw = 0.f;
     long long *Gc = A.G;
+    // The count column of rows 0..wc: differences (as the walks update it)
+    // to per-row add counts by a block-wide inclusive scan, and back. Each
+    // warp scans a segment of rows; segment totals are combined through
+    // shared memory. Called by every thread of the CTA.
+    auto counts_from_diffs = [&]() {
+        const int nw = (int)(blockDim.x >> 5), warp = tid >> 5, lane = tid & 31;
+        const int nr = wc + 1;
+        const int seg = ((nr + nw - 1) / nw + 31) & ~31;
+        const int r0 = warp * seg, r1 = min(r0 + seg, nr);
+        int carry = 0;
+        for (int r = r0; r < r1; r += 32) {
+            const int rr = r + lane;
+            int x = rr < r1 ? tile[rr * TS + CNT] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            x += carry;
+            if (rr < r1) tile[rr * TS + CNT] = x;
+            carry = __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) s_wsum[warp] = carry;
+        __syncthreads();
+        int off = 0;
+        for (int w2 = 0; w2 < warp; ++w2) off += s_wsum[w2];
+        if (off != 0)
+            for (int rr = r0 + lane; rr < r1; rr += 32) tile[rr * TS + CNT] += off;
+        __syncthreads();
+    };
+    auto diffs_from_counts = [&]() {
+        const int nw = (int)(blockDim.x >> 5), warp = tid >> 5, lane = tid & 31;
+        const int nr = wc + 1;
+        const int seg = ((nr + nw - 1) / nw + 31) & ~31;
+        const int r0 = warp * seg, r1 = min(r0 + seg, nr);
+        // the count before the segment belongs to another warp: read it first
+        const int prev0 = (r0 > 0 && r0 < r1) ? tile[(r0 - 1) * TS + CNT] : 0;
+        __syncthreads();
+        if (r1 > r0) {
+            // chunks last to first, so each chunk's predecessor is still a count
+            for (int r = r0 + (((r1 - r0 - 1) >> 5) << 5); r >= r0; r -= 32) {
+                const int rr = r + lane;
+                const int x = rr < r1 ? tile[rr * TS + CNT] : 0;
+                int pv = __shfl_up_sync(0xffffffffu, x, 1);
+                if (lane == 0) pv = (r == r0) ? prev0 : tile[(r - 1) * TS + CNT];
+                if (rr < r1) tile[rr * TS + CNT] = x - pv;
+            }
+        }
+        __syncthreads();
+    };
+    // Value of a tile entry since its last flush: raw sum minus count * M
+    // (modulo 2^32; the bounds keep the true value below 2^31 in magnitude).
+    auto entry_value = [&](int j, int s) -> int {
+        const unsigned n_add = (unsigned)tile[j * TS + CNT];
+        return (int)((unsigned)tile[j * TS + s] - n_add * (unsigned)kMagicBits);
+    };
     // moves the int32 tile of the current model into its int64 partial slot
     auto flush_tile = [&]() {
+        counts_from_diffs();
         for (int i = tid; i < A.n_orb * wc; i += blockDim.x) {
             const int s = i / wc, j = i - s * wc;
-            const int v = tile[j * TS + s];
+            const int v = entry_value(j, s);
             if (v)
                 atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j),
                           static_cast<unsigned long long>(static_cast<long long>(v)));
@@ -464,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // per model for a batch (CTAs flush into it with integer atomics)
             const long slot = (MAXM == 1) ? (long)chunk * gridDim.x + blockIdx.x : (long)mi;
             Gc = A.G + slot * (long)A.n_orb * A.chunk_w;
-            for (int i = tid; i < TS * A.chunk_w; i += blockDim.x) tile[i] = 0;
+            for (int i = tid; i < TS * (A.chunk_w + 1); i += blockDim.x) tile[i] = 0;
             for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
             const int n_om = (MODE == TETRA_POINT) ? wc : wc + 1;
             for (int i = tid; i < n_om; i += blockDim.x) om[i] = M.omega[w0 + i];
@@ -491,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncthreads();
         }
         const int st = k & 1;
-        for (int i = tid; i < kKBins + 32 * A.n_classes; i += blockDim.x) (i < kKBins ? khist[i] : chist[i - kKBins]) = 0;
+        for (int i = tid; i < kKBins; i += blockDim.x) khist[i] = 0;
         if (tid == 0) s_slot = 0;
         const bool ok = mbar_wait_bounded(&mbar[st], (k >> 1) & 1, A.status);
         if (__syncthreads_or(!ok)) {
@@ -502,6 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const WT *Ws = reinterpret_cast<const WT *>(stage[st] + A.w_box_off);
         const int ix = box % M.nbx, iy = (box / M.nbx) % M.nby, iz = box / (M.nbx * M.nby);
         const int gx0 = ix * A.BX, gy0 = iy * A.BY, gz0 = M.z0 + iz * A.BZ;
+        const int lane = tid & 31, warp = tid >> 5, nwarp = (int)(blockDim.x >> 5);
 
         // Bmax = max |w| over the staged box (all of it, padding included, so it
         // bounds every orbital weight an item can read)
@@ -524,156 +597,127 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
+        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        if (lane == 0) red_f[warp] = bmax;
 
-        // Pass A: window of every item (corner min / max only), histogram of its
-        // length K, so that pass B can hand items of similar length to the same
-        // warp. The integers an item adds do not depend on which thread adds
-        // them, so the grouping cannot change the result.
-        for (int it = tid; it < A.items_per_box; it += blockDim.x) {
-            const int cube = it & (ncube - 1);
-            const int rest = it >> lcube;
-            const int t = rest % 6, n = rest / 6;
-            const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
+        // Pass A: window of every item (corner min / max only) and a histogram
+        // of its length K, so that pass B can hand items of similar length to
+        // the same warp. The integers an item adds do not depend on which thread
+        // adds them, so the grouping cannot change the result.
+        for (int base = warp * 32; base < A.items_per_box; base += nwarp * 32) {
+            const int it = base + lane;
             int K = 0, lo = 0;
-            if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
-                float e1 = 3.0e38f, e4 = -3.0e38f;
-                const uint32_t code = tet_code(t);
-                const int p0 = cx + PX * (cy + PY * cz);
+            if (it < A.items_per_box) {
+                const int cube = it & (ncube - 1);
+                const int rest = it >> lcube;
+                const int t = rest % 6, n = rest / 6;
+                const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
+                if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
+                    float e1 = 3.0e38f, e4 = -3.0e38f;
+                    const uint32_t code = tet_code(t);
+                    const int p0 = cx + PX * (cy + PY * cz);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int p = p0 + s_cdelta[(code >> (3 * q)) & 7];
-                    const float ev = Es[p * A.eps_stride + n];
-                    e1 = fminf(e1, ev);
-                    e4 = fmaxf(e4, ev);
+                    for (int q = 0; q < 4; ++q) {
+                        const int p = p0 + s_cdelta[(code >> (3 * q)) & 7];
+                        const float ev = Es[p * A.eps_stride + n];
+                        e1 = fminf(e1, ev);
+                        e4 = fmaxf(e4, ev);
+                    }
+                    int hi;
+                    item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, M.n_omega, lo, hi);
+                    K = max(0, hi - lo + 1);
                 }
-                int hi;
-                item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, M.n_omega, lo, hi);
-                K = max(0, hi - lo + 1);
+                s_lo[it] = (short)(lo - w0);
+                s_K[it] = (unsigned short)K;
             }
-            s_lo[it] = (short)(lo - w0);
-            s_K[it] = (unsigned short)K;
             if (K > 0) atomicAdd(&khist[min(K, kKBins - 1)], 1);
         }
-        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-        if ((tid & 31) == 0) red_f[tid >> 5] = bmax;
         __syncthreads();
-        // Items ranked by window length K: exclusive scan of the K histogram
+        // Items ranked by window length K: an exclusive scan of the K histogram
         // gives each length its first rank; an item's rank = first rank + its
         // place among items of equal K (atomic cursor; items of equal K are
-        // interchangeable). Rank / 96 is the item's length class.
+        // interchangeable).
         if (tid < 32) {
             constexpr int PER = kKBins / 32;
-            int v[PER], s = 0;
+            int v[PER], sum = 0;
 #pragma unroll
-            for (int j = 0; j < PER; ++j) { v[j] = khist[tid * PER + j]; s += v[j]; }
-            int x = s;
+            for (int j = 0; j < PER; ++j) { v[j] = khist[tid * PER + j]; sum += v[j]; }
+            int x = sum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, x, o);
                 if (tid >= o) x += y;
             }
-            int run = x - s;
+            int run = x - sum;
 #pragma unroll
             for (int j = 0; j < PER; ++j) { kcursor[tid * PER + j] = run; run += v[j]; }
             if (tid == 31) s_active = x;
         }
-        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-        if ((tid & 31) == 0) red_f[tid >> 5] = bmax;
-        __syncthreads();
-        for (int it = tid; it < A.items_per_box; it += blockDim.x) {
-            const int K = s_K[it];
-            if (K > 0) {
-                const int rank = atomicAdd(&kcursor[min(K, kKBins - 1)], 1);
-                const int cls = rank / kClassSize;
-                s_cls[it] = (unsigned char)cls;
-                atomicAdd(&chist[cls * 32 + (s_lo[it] & 31)], 1);
-            }
-        }
-        __syncthreads();
-        // residue-major order inside each class
-        {
-            const int lane = tid & 31;
-            for (int c = tid >> 5; c < A.n_classes; c += (int)(blockDim.x >> 5)) {
-                const int v = chist[c * 32 + lane];
-                int x = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                ccursor[c * 32 + lane] = c * kClassSize + x - v;
-            }
-        }
         bmax = 0.f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) bmax = fmaxf(bmax, red_f[i]);
+        for (int i = 0; i < nwarp; ++i) bmax = fmaxf(bmax, red_f[i]);
         __syncthreads();
-        for (int it = tid; it < A.items_per_box; it += blockDim.x) {
-            if (s_K[it] > 0)
-                s_list[atomicAdd(&ccursor[s_cls[it] * 32 + (s_lo[it] & 31)], 1)] = (unsigned short)it;
+        for (int base = warp * 32; base < A.items_per_box; base += nwarp * 32) {
+            const int it = base + lane;
+            const int K = it < A.items_per_box ? (int)s_K[it] : 0;
+            if (K > 0) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
         }
         __syncthreads();
         const int n_active = s_active;
-        const int n_slots = 3 * ((n_active + kClassSize - 1) / kClassSize);
+        const int n_slots = (n_active + 31) >> 5;
 
-        // Pass B: warp g (0..2) of a class takes the class's items g, g+3, g+6, ...
-        // A class holds 96 items of nearly equal window length, so the lanes
-        // finish together; it is residue-major, so the 32 lanes get windows that
-        // start on (nearly) distinct tile rows mod 32 and their shared-memory
-        // atomics hit distinct banks at every step.
-        // Warps claim the slots longest-window class first (a shared counter),
-        // which balances the warps' work before the end-of-box barrier.
-        const int lane = tid & 31;
+        // Pass B: slot q holds the 32 items of ranks 32q .. 32q+31 (nearly equal
+        // window length, so a warp's lanes finish together). Warps claim slots
+        // longest windows first (a shared counter), which balances the warps'
+        // work before the end-of-box barrier.
         for (;;) {
             int claim = 0;
             if (lane == 0) claim = atomicAdd(&s_slot, 1);
             claim = __shfl_sync(0xffffffffu, claim, 0);
             if (claim >= n_slots) break;
-            const int slot = n_slots - 1 - claim;
-            const int c = slot / 3;
-            const int pos = c * kClassSize + (slot - 3 * c) + 3 * lane;
-            if (pos >= n_active) continue;
-            const int it = s_list[pos];
+            const int pos = (n_slots - 1 - claim) * 32 + lane;
+            const bool valid = pos < n_active;
+            const int it = valid ? (int)s_list[pos] : 0;
             const int cube = it & (ncube - 1);
             const int rest = it >> lcube;
             const int t = rest % 6, n = rest / 6;
             const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
+            const int p0 = cx + PX * (cy + PY * cz);
+            const int lo = valid ? w0 + s_lo[it] : w0;
+            const int hi = valid ? lo + s_K[it] - 1 : w0 - 1;
             float e[4];
             int p[4];
             const uint32_t code = tet_code(t);
-            const int p0 = cx + PX * (cy + PY * cz);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 p[q] = p0 + s_cdelta[(code >> (3 * q)) & 7];
                 e[q] = Es[p[q] * A.eps_stride + n];
             }
-            cswap(e[0], e[1], p[0], p[1]);
-            cswap(e[2], e[3], p[2], p[3]);
-            cswap(e[0], e[2], p[0], p[2]);
-            cswap(e[1], e[3], p[1], p[3]);
-            cswap(e[1], e[2], p[1], p[2]);
-            const int lo = w0 + s_lo[it];
-            const int hi = lo + s_K[it] - 1;
+            sort4(e, p);
             float b[4][NORB];
 #pragma unroll
             for (int r4 = 0; r4 < 4; ++r4)
                 load_weights<NORB, WT>(Ws + (long)p[r4] * A.w_stride + n * A.n_orb, A.n_orb, b[r4]);
-            // per-item bound on every |contribution|, in fixed-point units
-            float qmax;
-            if (MODE == TETRA_POINT)
-                qmax = bmax * 4.f * fq * 3.1f * safe_rcp(e[3] - e[0]);
-            else
-                qmax = bmax * 4.f * fq * max_iw * 1.01f;
+            // per-item bound on every |contribution|, in fixed-point units (the
+            // tetrahedron DOS is at most 3/E41 of V_T/V_G; a bin average at most
+            // its weight step over the narrowest bin)
+            float qmax = (MODE == TETRA_POINT) ? bmax * 4.f * fq * 3.1f * safe_rcp(e[3] - e[0])
+                                               : bmax * 4.f * fq * max_iw * 1.01f;
             if (!(e[3] > e[0])) qmax = 3.0e38f;
             const bool fast = qmax < (float)A.fast_cap;
             const uint32_t gcube = (uint32_t)(gx0 + cx) +
                                    (uint32_t)M.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)M.n2 * (uint32_t)(gz0 + cz));
             const float dith = item_dither((gcube * 6u + (uint32_t)t) * (uint32_t)A.nb + (uint32_t)n);
+            if (!valid) continue;
+            // Bookkeeping of the tile: every entry of blocks lo/64 .. hi/64 may
+            // receive at most qmax from this item, and rows lo .. hi each receive
+            // one add per orbital.
             if (fast) {
-                // every tile entry of these blocks may receive at most qmax from this item
-                const unsigned qb = (unsigned)qmax + 2u;
-                for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qb);
+                const unsigned qbnd = (unsigned)qmax + 2u;
+                for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
+                atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
+                atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
             }
-            if (MODE == TETRA_POINT) {
+            if constexpr (MODE == TETRA_POINT) {
                 TetP TP;
                 tetp_setup(TP, e[0], e[1], e[2], e[3], fq);
                 if (fast) {
@@ -693,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             acc = fmaf(b[1][s], d[1], acc);
                             acc = fmaf(b[2][s], d[2], acc);
                             acc = fmaf(b[3][s], d[3], acc);
-                            atomicAdd(col + s, __float_as_int(acc + kMagic) - kMagicBits);
+                            atomicAdd(col + s, __float_as_int(acc + kMagic));
                         }
                         i = (i == hi) ? lo : i + 1;
                     }
@@ -723,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             acc = fmaf(b[1][s], d[1], acc);
                             acc = fmaf(b[2][s], d[2], acc);
                             acc = fmaf(b[3][s], d[3], acc);
-                            atomicAdd(col + s, __float_as_int(acc + kMagic) - kMagicBits);
+                            atomicAdd(col + s, __float_as_int(acc + kMagic));
                         }
                     } else {
                         deposit_slow<NORB>(b, d, A.n_orb, dith, Gc + (i - w0), A.chunk_w, A.status);
@@ -737,28 +781,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async_smem();
             issue(k + 2, st);
         }
-        // A block whose bound reached kFlushAt is moved into the CTA's int64
+        // A block whose bound reached flush_at is moved into the CTA's int64
         // partial before the next box: one box adds less than 2^30 - 2^20 to any
-        // entry (per-item cap x items per box), so entries stay below 2^31.
-        const bool mine = tid < n_blk && blk_bound[tid] >= kFlushAt;
+        // entry (per-unit cap x units per box), so entries stay below 2^31.
+        // A flushed entry is reset to count * M, the raw value of zero.
+        const bool mine = tid < n_blk && blk_bound[tid] >= A.flush_at;
         if (__syncthreads_or(mine)) {
+            counts_from_diffs();
             for (int bk = 0; bk < n_blk; ++bk) {
-                if (blk_bound[bk] < kFlushAt) continue;   // uniform: every thread reads the same value
+                if (blk_bound[bk] < A.flush_at) continue;   // uniform: every thread reads the same value
                 const int j0 = bk << 6, jn = min(64, wc - j0);
                 for (int i = tid; i < A.n_orb * 64; i += blockDim.x) {
                     const int s = i >> 6, j = i & 63;
                     if (j >= jn) continue;
-                    int *e = tile + (j0 + j) * TS + s;
-                    const int v = *e;
+                    const int v = entry_value(j0 + j, s);
                     if (v) {
                         atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j0 + j),
                                   static_cast<unsigned long long>(static_cast<long long>(v)));
-                        *e = 0;
+                        tile[(j0 + j) * TS + s] = (int)((unsigned)tile[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
                     }
                 }
             }
             __syncthreads();
-            if (tid < n_blk && blk_bound[tid] >= kFlushAt) blk_bound[tid] = 0;
+            diffs_from_counts();
+            if (tid < n_blk && blk_bound[tid] >= A.flush_at) blk_bound[tid] = 0;
             __syncthreads();
         }
     }
@@ -855,7 +901,6 @@ void fill_common(const Plan &P, FwdArgs &A) {
     A.nb = P.d.n_bands; A.n_orb = P.d.n_orb;
     A.BX = P.BX; A.BY = P.BY; A.BZ = P.BZ;
     A.lbx = __builtin_ctz(P.BX); A.lby = __builtin_ctz(P.BY); A.lbz = __builtin_ctz(P.BZ);
-    A.n_classes = (P.items_per_box + 95) / 96;
     A.eps_stride = P.eps_stride; A.w_stride = P.w_stride;
     const uint32_t npts = (uint32_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
     A.e_box_bytes = npts * P.eps_stride * 4u;
@@ -865,6 +910,7 @@ void fill_common(const Plan &P, FwdArgs &A) {
     A.stage_bytes = (A.w_box_off + A.w_box_bytes + 127u) & ~127u;
     A.chunk_w = P.chunk_w;
     A.items_per_box = P.items_per_box;
+    A.flush_at = 1u << P.flush_bits;
     long cap = ((1L << 30) - (1L << 20)) / A.items_per_box;
     if (cap > (1L << 21)) cap = 1L << 21;
     A.fast_cap = (int)cap;

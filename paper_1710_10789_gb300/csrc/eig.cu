@@ -60,14 +60,34 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
                 W[a + 1][s] = sw ? u : v;
             }
         }
+    // Stores: 16-byte vectors when a point's values fill whole vectors (the
+    // layout's point strides are multiples of 16 bytes), scalars otherwise.
     float *eo = A.eps + p * A.eps_stride;
+    if constexpr (N % 4 == 0) {
 #pragma unroll
-    for (int n = 0; n < N; ++n) eo[n] = ev[n];
+        for (int n = 0; n < N; n += 4)
+            *reinterpret_cast<float4 *>(eo + n) = make_float4(ev[n], ev[n + 1], ev[n + 2], ev[n + 3]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < N; ++n) eo[n] = ev[n];
+    }
     WT *wo = static_cast<WT *>(A.w) + p * A.w_stride;
+    constexpr int VEC = 16 / sizeof(WT);
+    if constexpr ((N * N) % VEC == 0) {
 #pragma unroll
-    for (int n = 0; n < N; ++n)
+        for (int v = 0; v < N * N / VEC; ++v) {
+            uint4 q;
+            WT *e = reinterpret_cast<WT *>(&q);
 #pragma unroll
-        for (int s = 0; s < N; ++s) wo[n * N + s] = from_f32<WT>(W[n][s]);
+            for (int j = 0; j < VEC; ++j) e[j] = from_f32<WT>(W[(v * VEC + j) / N][(v * VEC + j) % N]);
+            reinterpret_cast<uint4 *>(wo)[v] = q;
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < N; ++n)
+#pragma unroll
+            for (int s = 0; s < N; ++s) wo[n * N + s] = from_f32<WT>(W[n][s]);
+    }
 }
 
 template <int N>

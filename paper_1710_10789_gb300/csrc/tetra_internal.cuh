@@ -25,7 +25,8 @@ struct tetra_plan_s {
     int grid_x;                 // persistent CTAs per energy chunk
     int threads;
     int fixed_bits;             // fixed-point fraction bits (see dos.cu)
-    int items_per_box;          // (tetrahedron, band) items per box
+    int flush_bits;             // a tile block is flushed once its bound reaches 2^flush_bits
+    int items_per_box;          // work units per box: (pair, band) in point mode, (tetrahedron, band) in bin mode
     int tile_stride;            // ints per energy in the shared tile
     size_t smem_bytes;
 };

@@ -190,6 +190,23 @@ def test_bitwise_determinism_and_launch_shape_independence(T, monkeypatch):
     assert np.array_equal(g1, g3)
 
 
+@pytest.mark.parametrize("mode", ["point", "bin"])
+def test_tile_flushes_leave_the_bits_unchanged(T, monkeypatch, mode):
+    """Blocks of the shared tile are moved into the int64 partials when their
+    bound passes 2^flush_bits (2^30 normally). With a low threshold every
+    box flushes; integer accumulation makes the result bit-identical, which
+    checks the raw-sum / add-count bookkeeping of the flush."""
+    n = (20, 18, 16)
+    _, eps, w = tb_problem(8, n)
+    omega = energy_window(eps, 700 if mode == "point" else 301)   # bin mode: edges
+    g1, *_ = run_gpu(T, eps, w, n, omega, mode=mode)
+    monkeypatch.setenv("TETRA_FLUSH_BITS", "10")
+    g2, *_ = run_gpu(T, eps, w, n, omega, mode=mode)
+    assert np.array_equal(g1, g2)
+    r = oracle.dos(eps, w, *n, omega.astype(np.float64), mode=mode, nthreads=NTHREADS)
+    assert_parity(g2, r)
+
+
 def test_z_slabs_add_up_to_the_whole(T, monkeypatch):
     """Splitting the grid into k-slabs (the unit of multi-device sharding):
     with a common fixed-point unit every item contributes the same integers,
