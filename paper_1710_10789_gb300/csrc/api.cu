@@ -89,7 +89,10 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     const size_t npts = (size_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
     const size_t e_off = (npts * P.eps_stride * 4 + 127) & ~size_t(127);
     const size_t stage = (e_off + npts * P.w_stride * P.wbytes + 127) & ~size_t(127);
-    P.items_per_box = 6 * P.BX * P.BY * P.BZ * d.n_bands;
+    // point mode with up to 8 orbitals: one item per face-sharing tetrahedron
+    // pair (3 per cube); otherwise one item per tetrahedron (6 per cube)
+    const bool pairs = d.mode == TETRA_POINT && tetra::norb_template(d.n_orb) <= 8;
+    P.items_per_box = (pairs ? 3 : 6) * P.BX * P.BY * P.BZ * d.n_bands;
     if (P.items_per_box > 65535) return TETRA_EUNSUPPORTED;
     P.tile_stride = tetra::norb_template(d.n_orb) + 1;
     // two TMA stages, per-item sort arrays, length histogram and cursors,
@@ -104,7 +107,7 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     P.n_chunks = (d.n_omega + cw - 1) / cw;
     P.chunk_w = (d.n_omega + P.n_chunks - 1) / P.n_chunks;
     P.smem_bytes = fixed + per_w * P.chunk_w + 8;
-    P.threads = 512;
+    P.threads = pairs ? 384 : 512;
     const int ctas = std::max(1, ctas_per_sm) * P.sm_count;
     P.grid_x = std::max(1, std::min(P.n_boxes, (ctas + P.n_chunks - 1) / P.n_chunks));
     // Fixed-point fraction bits. A DOS value is a sum of N contributions of

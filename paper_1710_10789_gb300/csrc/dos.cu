@@ -17,6 +17,11 @@
 //    positions (Sec. II.C sorts E1 <= E2 <= E3 <= E4), reads the orbital
 //    weights in sorted order, and visits only the energies strictly inside
 //    (E1, E4) (bins overlapping it in bin mode); all others get zero weight.
+//  * Point mode (up to 8 orbitals): the item is a pair of tetrahedra sharing
+//    a face (Table I's six form three such pairs). Their windows overlap
+//    heavily, so one walk over the union of the two windows adds both
+//    tetrahedra's contributions at each energy before touching the shared
+//    tile: about half the shared-memory traffic of one tetrahedron each.
 //  * Items of a box are ranked by window length (counting sort), so the 32
 //    lanes of a warp walk windows of nearly equal length.
 //  * Each visited energy adds sum_l b_{l,s} dw_l to the CTA's tile for every
@@ -53,7 +58,20 @@ namespace {
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float + kMagic rounds to an integer
 constexpr int kMagicBits = 0x4B400000;  // bit pattern of kMagic
 constexpr uint32_t kSmemAlign = 1024;
-constexpr int kThreads = 512;
+// Work unit, threads per CTA and registers per thread. Point mode with up to
+// 8 orbitals walks face-sharing tetrahedron pairs, holding two tetrahedra's
+// weights and constants in registers; 16 orbitals would not fit, so there, as
+// in bin mode, a unit is one tetrahedron. Each of the SM's four
+// sub-partitions has 16K registers for its warps: 12 warps (3 per
+// sub-partition) can use 168 registers per thread, 16 warps 128.
+template <int MODE, int NORB>
+struct Cfg {
+    static constexpr bool pairs = MODE == TETRA_POINT && NORB <= 8;
+    static constexpr int threads = pairs ? 384 : 512;
+    static constexpr int max_regs = pairs ? 168 : 128;
+    static constexpr int units_per_cube = pairs ? 3 : 6;
+};
+constexpr int kMaxThreads = 512;
 constexpr int kKBins = 256;     // window-length histogram bins (K >= 255 share one)
 
 // Table I, corner labels minus one; label c sits at offset (c&1, (c>>1)&1, (c>>2)&1).
@@ -72,6 +90,19 @@ __device__ __forceinline__ uint32_t tet_code(int t) {
     return t < 5 ? (uint32_t)(kTetLo >> (12 * t)) & 0xFFFu : kTetHi;
 }
 
+// Table I's tetrahedra as three face-sharing pairs: (1st, 2nd), (3rd, 5th),
+// (4th, 6th). Per pair five corner labels minus one: the three corners of the
+// shared face, the corner only in the first tetrahedron, the corner only in
+// the second. First tetrahedron = slots {0,1,2,3}, second = slots {0,1,2,4}.
+constexpr int kPair[3][5] = {{1, 2, 5, 0, 3}, {2, 4, 5, 0, 6}, {2, 5, 7, 3, 6}};
+constexpr uint32_t pack_pair(int p) {
+    return (uint32_t)(kPair[p][0] | kPair[p][1] << 3 | kPair[p][2] << 6 | kPair[p][3] << 9 |
+                      kPair[p][4] << 12);
+}
+constexpr uint64_t kPairCode = (uint64_t)pack_pair(0) | (uint64_t)pack_pair(1) << 16 |
+                               (uint64_t)pack_pair(2) << 32;
+__device__ __forceinline__ uint32_t pair_code(int p) { return (uint32_t)(kPairCode >> (16 * p)) & 0x7FFFu; }
+
 // Launch constants shared by every model of a launch.
 struct FwdArgs {
     int nb, n_orb;
@@ -80,7 +111,7 @@ struct FwdArgs {
     int eps_stride, w_stride;
     uint32_t e_box_bytes, w_box_bytes, w_box_off, stage_bytes;   // w box at stage + w_box_off (128-aligned)
     int chunk_w;         // energies per shared tile (largest model of a batch)
-    int items_per_box;   // (tetrahedron, band) items per box
+    int items_per_box;   // items per box: (pair, band) in point mode, (tetrahedron, band) otherwise
     int fast_cap;
     unsigned flush_at;   // a 64-energy block is flushed once its bound reaches this
     long long *G;        // int64 partials, [slot][n_orb][chunk_w]
@@ -105,6 +136,19 @@ __device__ __forceinline__ void cswap(float &ea, float &eb, int &pa, int &pb) {
     const float lo = s ? eb : ea, hi = s ? ea : eb;
     const int plo = s ? pb : pa, phi = s ? pa : pb;
     ea = lo; eb = hi; pa = plo; pb = phi;
+}
+
+// One rounded contribution added to the CTA's int64 partial (global 64-bit
+// integer atomics): the path of the rare items whose bound does not fit the
+// int32 tile. acc holds the dithered value; the same single rounding to
+// nearest as the tile path.
+__device__ __forceinline__ void deposit_one(float acc, long long *g, int *status) {
+    if (fabsf(acc) < 9.0e18f) {
+        const long long q = __float2ll_rn(acc);
+        if (q != 0) atomicAdd(reinterpret_cast<unsigned long long *>(g), static_cast<unsigned long long>(q));
+    } else {
+        atomicOr(status, kFlagRange);
+    }
 }
 
 __device__ __forceinline__ void sort4(float (&e)[4], int (&p)[4]) {
@@ -348,7 +392,7 @@ struct Batch {
 };
 
 template <int NORB, typename WT, int MODE, int MAXM>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     tetra_dos_fwd_kernel(const __grid_constant__ Batch<MAXM> B, const FwdArgs A) {
     // tile row: NORB orbitals + the row's add count (differences); the odd
     // row length also spreads consecutive rows over the shared-memory banks
@@ -376,8 +420,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     int *kcursor = khist + kKBins;           // rank cursors per window length
     uint64_t *mbar = reinterpret_cast<uint64_t *>(
         (reinterpret_cast<uintptr_t>(kcursor + kKBins) + 15) & ~uintptr_t(15));
-    __shared__ float red_f[kThreads / 32];
-    __shared__ int s_wsum[kThreads / 32];
+    __shared__ float red_f[kMaxThreads / 32];
+    __shared__ int s_wsum[kMaxThreads / 32];
     __shared__ int s_abort, s_active, s_slot;
     __shared__ int s_cdelta[8];   // staged-box point offset of cube corner c
 
@@ -608,16 +652,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int it = base + lane;
             int K = 0, lo = 0;
             if (it < A.items_per_box) {
+                constexpr bool PAIRS = Cfg<MODE, NORB>::pairs;
+                constexpr int UPC = Cfg<MODE, NORB>::units_per_cube;
                 const int cube = it & (ncube - 1);
                 const int rest = it >> lcube;
-                const int t = rest % 6, n = rest / 6;
+                const int t = rest % UPC, n = rest / UPC;
                 const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
                 if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
+                    // a pair's window is the union of its two tetrahedra's: the
+                    // window of the min / max over its five corners
                     float e1 = 3.0e38f, e4 = -3.0e38f;
-                    const uint32_t code = tet_code(t);
+                    const uint32_t code = PAIRS ? pair_code(t) : tet_code(t);
                     const int p0 = cx + PX * (cy + PY * cz);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < (PAIRS ? 5 : 4); ++q) {
                         const int p = p0 + s_cdelta[(code >> (3 * q)) & 7];
                         const float ev = Es[p * A.eps_stride + n];
                         e1 = fminf(e1, ev);
@@ -679,11 +727,110 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int it = valid ? (int)s_list[pos] : 0;
             const int cube = it & (ncube - 1);
             const int rest = it >> lcube;
-            const int t = rest % 6, n = rest / 6;
             const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
             const int p0 = cx + PX * (cy + PY * cz);
             const int lo = valid ? w0 + s_lo[it] : w0;
             const int hi = valid ? lo + s_K[it] - 1 : w0 - 1;
+            const uint32_t gcube = (uint32_t)(gx0 + cx) +
+                                   (uint32_t)M.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)M.n2 * (uint32_t)(gz0 + cz));
+            if constexpr (Cfg<MODE, NORB>::pairs) {
+                if (!valid) continue;
+                // ---- a pair of tetrahedra sharing a face, walked over the union window
+                const int pr = rest % 3, n = rest / 3;
+                const uint32_t code = pair_code(pr);
+                float ea[4], eb[4];
+                int pa[4], pb[4];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    pa[q] = pb[q] = p0 + s_cdelta[(code >> (3 * q)) & 7];
+                    ea[q] = eb[q] = Es[pa[q] * A.eps_stride + n];
+                }
+                pa[3] = p0 + s_cdelta[(code >> 9) & 7];
+                pb[3] = p0 + s_cdelta[(code >> 12) & 7];
+                ea[3] = Es[pa[3] * A.eps_stride + n];
+                eb[3] = Es[pb[3] * A.eps_stride + n];
+                sort4(ea, pa);
+                sort4(eb, pb);
+                float ba[4][NORB], bb[4][NORB];
+#pragma unroll
+                for (int r4 = 0; r4 < 4; ++r4) {
+                    load_weights<NORB, WT>(Ws + (long)pa[r4] * A.w_stride + n * A.n_orb, A.n_orb, ba[r4]);
+                    load_weights<NORB, WT>(Ws + (long)pb[r4] * A.w_stride + n * A.n_orb, A.n_orb, bb[r4]);
+                }
+                // bound on every |contribution| of the pair, in fixed-point units:
+                // the tetrahedron DOS is at most 3/E41 of V_T/V_G; a flat
+                // tetrahedron (E1 = E4) contributes nothing in point mode
+                const float qa = (ea[3] > ea[0]) ? bmax * 4.f * fq * 3.1f * safe_rcp(ea[3] - ea[0]) : 0.f;
+                const float qb = (eb[3] > eb[0]) ? bmax * 4.f * fq * 3.1f * safe_rcp(eb[3] - eb[0]) : 0.f;
+                const float qmax = qa + qb;
+                const bool fast = qmax < (float)A.fast_cap;
+                const float dith = item_dither((gcube * 3u + (uint32_t)pr) * (uint32_t)A.nb + (uint32_t)n);
+                if (fast) {
+                    const unsigned qbnd = (unsigned)qmax + 2u;
+                    for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
+                    atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
+                    atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
+                }
+                TetP TA, TB;
+                tetp_setup(TA, ea[0], ea[1], ea[2], ea[3], fq);
+                tetp_setup(TB, eb[0], eb[1], eb[2], eb[3], fq);
+                // both tetrahedra's corner derivatives at E; zero outside a
+                // tetrahedron's own window (E1, E4)
+                auto both = [&](float E, float (&da)[4], float (&db)[4]) {
+                    tetp_dw(TA, E, da);
+                    tetp_dw(TB, E, db);
+                    const bool ia = E > TA.e1 && E < TA.e4;
+                    const bool ib = E > TB.e1 && E < TB.e4;
+#pragma unroll
+                    for (int r4 = 0; r4 < 4; ++r4) {
+                        da[r4] = ia ? da[r4] : 0.f;
+                        db[r4] = ib ? db[r4] : 0.f;
+                    }
+                };
+                if (fast) {
+                    // lane-dependent start, wrapping walk (see below)
+                    const int K = hi - lo + 1;
+                    int i = lo + ((lane * K) >> 5);
+                    for (int j = 0; j < K; ++j) {
+                        float da[4], db[4];
+                        both(om[i - w0], da, db);
+                        int *col = tile + (i - w0) * TS;
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            float acc = fmaf(ba[0][s], da[0], dith);
+                            acc = fmaf(ba[1][s], da[1], acc);
+                            acc = fmaf(ba[2][s], da[2], acc);
+                            acc = fmaf(ba[3][s], da[3], acc);
+                            acc = fmaf(bb[0][s], db[0], acc);
+                            acc = fmaf(bb[1][s], db[1], acc);
+                            acc = fmaf(bb[2][s], db[2], acc);
+                            acc = fmaf(bb[3][s], db[3], acc);
+                            atomicAdd(col + s, __float_as_int(acc + kMagic));
+                        }
+                        i = (i == hi) ? lo : i + 1;
+                    }
+                } else {
+                    for (int i = lo; i <= hi; ++i) {
+                        float da[4], db[4];
+                        both(om[i - w0], da, db);
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            if (s >= A.n_orb) continue;
+                            float acc = fmaf(ba[0][s], da[0], dith);
+                            acc = fmaf(ba[1][s], da[1], acc);
+                            acc = fmaf(ba[2][s], da[2], acc);
+                            acc = fmaf(ba[3][s], da[3], acc);
+                            acc = fmaf(bb[0][s], db[0], acc);
+                            acc = fmaf(bb[1][s], db[1], acc);
+                            acc = fmaf(bb[2][s], db[2], acc);
+                            acc = fmaf(bb[3][s], db[3], acc);
+                            deposit_one(acc, Gc + (long)s * A.chunk_w + (i - w0), A.status);
+                        }
+                    }
+                }
+                continue;
+            }
+            const int t = rest % 6, n = rest / 6;
             float e[4];
             int p[4];
             const uint32_t code = tet_code(t);
@@ -704,8 +851,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                : bmax * 4.f * fq * max_iw * 1.01f;
             if (!(e[3] > e[0])) qmax = 3.0e38f;
             const bool fast = qmax < (float)A.fast_cap;
-            const uint32_t gcube = (uint32_t)(gx0 + cx) +
-                                   (uint32_t)M.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)M.n2 * (uint32_t)(gz0 + cz));
             const float dith = item_dither((gcube * 6u + (uint32_t)t) * (uint32_t)A.nb + (uint32_t)n);
             if (!valid) continue;
             // Bookkeeping of the tile: every entry of blocks lo/64 .. hi/64 may
@@ -872,7 +1017,7 @@ cudaError_t launch_t(size_t smem, dim3 grid, const Batch<MAXM> &Bt, const FwdArg
             }
         }
     }
-    k<<<grid, kThreads, smem, stream>>>(Bt, A);
+    k<<<grid, Cfg<MODE, NORB>::threads, smem, stream>>>(Bt, A);
     return cudaGetLastError();
 }
 
