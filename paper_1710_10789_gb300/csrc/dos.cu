@@ -245,10 +245,13 @@ __device__ __forceinline__ void tetp_setup(TetP &T, float e1, float e2, float e3
     T.c[3][3] = -4.f * (k2r41 + k3r41 + k3r42);
 }
 
+// Valid at any E: outside (E1, E4) the clamped distance v = 0 makes every
+// derivative exactly zero (E >= E4 always takes the E4 - E form). At E = E3
+// the third case's form is used (equal to the second's by continuity).
 __device__ __forceinline__ void tetp_dw(const TetP &T, float E, float d[4]) {
-    const bool in1 = E <= T.e2;
-    const bool in3 = E > T.e3;
-    const float v = in1 ? E - T.e1 : T.e4 - E;
+    const bool in1 = E <= T.e2 && E < T.e4;
+    const bool in3 = !in1 && E >= T.e3;
+    const float v = fmaxf(in1 ? E - T.e1 : T.e4 - E, 0.f);
     const float P = in1 ? T.P1 : T.P3;
     const float S = in1 ? T.S1 : T.S3;
     const float ra = in1 ? T.r21 : T.r41, rb = in1 ? T.r31 : T.r42, rc = in1 ? T.r41 : T.r43;
@@ -774,18 +777,11 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 TetP TA, TB;
                 tetp_setup(TA, ea[0], ea[1], ea[2], ea[3], fq);
                 tetp_setup(TB, eb[0], eb[1], eb[2], eb[3], fq);
-                // both tetrahedra's corner derivatives at E; zero outside a
-                // tetrahedron's own window (E1, E4)
+                // both tetrahedra's corner derivatives at E (zero outside a
+                // tetrahedron's own window (E1, E4), see tetp_dw)
                 auto both = [&](float E, float (&da)[4], float (&db)[4]) {
                     tetp_dw(TA, E, da);
                     tetp_dw(TB, E, db);
-                    const bool ia = E > TA.e1 && E < TA.e4;
-                    const bool ib = E > TB.e1 && E < TB.e4;
-#pragma unroll
-                    for (int r4 = 0; r4 < 4; ++r4) {
-                        da[r4] = ia ? da[r4] : 0.f;
-                        db[r4] = ib ? db[r4] : 0.f;
-                    }
                 };
                 if (fast) {
                     // lane-dependent start, wrapping walk (see below)
