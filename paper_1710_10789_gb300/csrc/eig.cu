@@ -4,9 +4,10 @@
 // the tetra layout, halo points included.
 //
 // One thread owns one k-point: it builds H(k) = diag(onsite) +
-// sum_r [t_r e^{ik.R_r} + h.c.] from the model staged in shared memory, runs
-// cyclic complex Jacobi sweeps with the upper triangle of H and the full
-// eigenvector matrix in registers (all indices compile-time after unrolling),
+// sum_r [t_r e^{ik.R_r} + h.c.] from the model staged in shared memory,
+// reduces it to real tridiagonal form by Householder reflections and
+// diagonalises that by implicit-shift QR, with H, the accumulated unitary and
+// the tridiagonal in registers (all indices compile-time after unrolling),
 // then sorts the eigenpairs with a transposition network and stores
 // eps_n and |V_sn|^2.
 #include "eig_common.cuh"
@@ -33,19 +34,34 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
     const int px = (int)(p % A.nx), py = (int)((p / A.nx) % A.ny), pz = (int)(p / ((long)A.nx * A.ny));
     const int x = px % A.n1, y = py % A.n2, z = pz % A.n3;
 
-    Mat<N> M;
-    build_h<N>(M, s_par, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
-    jacobi<N>(M);
-
-    // eigenvalues and weights, sorted ascending (odd-even transposition network)
+    Herm<N> M;
+    {
+        Mat<N> H;   // upper triangle of H(k)
+        build_h<N>(H, s_par, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                M.ar[i][j] = H.hr[j][i];
+                M.ai[i][j] = (i == j) ? 0.f : -H.hi[j][i];
+            }
+    }
     float ev[N];
     float W[N][N];   // W[n][s] = |V_sn|^2
+    if constexpr (N == 1) {
+        ev[0] = M.ar[0][0];
+        W[0][0] = 1.f;
+    } else {
+        householder_tridiag<N>(M);
+        tridiag_qr<N>(M);
 #pragma unroll
-    for (int n = 0; n < N; ++n) {
-        ev[n] = M.hr[n][n];
+        for (int n = 0; n < N; ++n) {
+            ev[n] = M.d[n];
 #pragma unroll
-        for (int s = 0; s < N; ++s) W[n][s] = M.vr[s][n] * M.vr[s][n] + M.vi[s][n] * M.vi[s][n];
+            for (int s = 0; s < N; ++s) W[n][s] = M.qr[s][n] * M.qr[s][n] + M.qi[s][n] * M.qi[s][n];
+        }
     }
+    // eigenvalues and weights, sorted ascending (odd-even transposition network)
 #pragma unroll
     for (int round = 0; round < N; ++round)
 #pragma unroll
