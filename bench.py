@@ -1,7 +1,7 @@
 """Benchmark of the linear tetrahedron orbital-resolved DOS on GB300.
 
 One step = the whole hot path on one synthetic tight-binding model: H(k) and
-the batched Jacobi eigensolve on the GPU (tetra_eig), then the orbital-resolved
+the batched Hermitian eigensolve on the GPU (tetra_eig), then the orbital-resolved
 DOS by the linear tetrahedron method (tetra_dos). Default workload: seeded
 8-orbital tetragonal model, 256^3 k-grid (100.7M tetrahedra), 8 bands,
 8 orbitals, 4000 energies on [eps_min - 0.1, eps_max + 0.1], FP32 weights,

@@ -167,8 +167,9 @@ typedef struct {
 
 /* Band energies and orbital weights of a tight-binding model on the plan's
  * grid (Sec. II.A: diagonalisation of H(k) point by point), written directly
- * in the tetra layout. A batched cyclic Jacobi eigensolver on the GPU; bands
- * ascending, w[n][s] = |V_{s n}|^2 stored in the plan's weight_dtype.
+ * in the tetra layout. A batched Hermitian eigensolver on the GPU (Householder
+ * reduction to real tridiagonal form, implicit-shift QR), one k-point per
+ * thread; bands ascending, w[n][s] = |V_{s n}|^2 stored in the plan's weight_dtype.
  * Requires plan n_bands == model n_orb <= 8. Halo points are written too. For
  * a slab plan (z_begin, z_end) only the point planes z_begin .. z_end (the
  * corners of its cubes) are written; the rest of eps and w is left as is. */

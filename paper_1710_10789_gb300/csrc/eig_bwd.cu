@@ -61,21 +61,40 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
         const bool live = k < nk;
         if (live) {
             const int x = (int)(k % A.n1), y = (int)((k / A.n1) % A.n2), z = (int)(k / ((long)A.n1 * A.n2));
-            Mat<N> M;
-            build_h<N>(M, s_par, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
-            jacobi<N>(M);
+            // the forward's eigensolver (Householder + implicit QR), so the
+            // eigenvectors are the ones the forward's weights came from
+            Herm<N> M;
+            {
+                Mat<N> H;
+                build_h<N>(H, s_par, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) {
+                        M.ar[i][j] = H.hr[j][i];
+                        M.ai[i][j] = (i == j) ? 0.f : -H.hi[j][i];
+                    }
+            }
             float lam[N];
+            if constexpr (N == 1) {
+                lam[0] = M.ar[0][0];
+                V[0] = 1.f;
+                V[1] = 0.f;
+            } else {
+                householder_tridiag<N>(M);
+                tridiag_qr<N>(M);
 #pragma unroll
-            for (int j = 0; j < N; ++j) lam[j] = M.hr[j][j];
+                for (int j = 0; j < N; ++j) lam[j] = M.d[j];
 #pragma unroll
-            for (int s = 0; s < N; ++s)
+                for (int s = 0; s < N; ++s)
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    V[2 * (s * N + j)] = M.vr[s][j];
-                    V[2 * (s * N + j) + 1] = M.vi[s][j];
-                }
-            // sorted band index of each Jacobi column (ties keep column order,
-            // as the forward's stable transposition sort does)
+                    for (int j = 0; j < N; ++j) {
+                        V[2 * (s * N + j)] = M.qr[s][j];
+                        V[2 * (s * N + j) + 1] = M.qi[s][j];
+                    }
+            }
+            // sorted band index of each eigenvector column (ties keep column
+            // order, as the forward's stable transposition sort does)
             int rank[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) {

@@ -1,5 +1,6 @@
 // Device code shared by the eigensolver and its adjoint: H(k) of the
-// tight-binding model (Eq. (1) in hopping form) and cyclic complex Jacobi.
+// tight-binding model (Eq. (1) in hopping form) and a Hermitian eigensolver
+// (Householder reduction to real tridiagonal form, implicit-shift QR).
 #pragma once
 #include "tetra_internal.cuh"
 
@@ -23,156 +24,7 @@ struct EigArgs {
 template <int N>
 struct Mat {
     float hr[N][N], hi[N][N];   // upper triangle of H used (i <= j)
-    float vr[N][N], vi[N][N];   // eigenvectors in columns
-    float skip;                 // couplings at or below this are dropped unrotated
 };
-
-// Full-matrix element H_kp from upper-triangle storage (k != p).
-template <int N>
-__device__ __forceinline__ void hget(const Mat<N> &M, int k, int p, float &re, float &im) {
-    if (k < p) { re = M.hr[k][p]; im = M.hi[k][p]; }
-    else { re = M.hr[p][k]; im = -M.hi[p][k]; }
-}
-template <int N>
-__device__ __forceinline__ void hset(Mat<N> &M, int k, int p, float re, float im) {
-    if (k < p) { M.hr[k][p] = re; M.hi[k][p] = im; }
-    else { M.hr[p][k] = re; M.hi[p][k] = -im; }
-}
-
-// Jacobi rotation zeroing H_pq (p < q): H <- U^H H U, V <- V U with
-// U_pp = c, U_pq = s, U_qp = -s e^{-i phi}, U_qq = c e^{-i phi}, H_pq = |h| e^{i phi}.
-struct Rot {
-    float c, s, er, ei;   // cos, sin, e^{-i phi}
-};
-
-// Parameters of the rotation for (p, q) from the current H; sets the new
-// H_pp, H_qq and zeroes H_pq. A coupling at the FP32 rounding level of ||H||
-// is dropped and the rotation becomes the identity (c = 1, s = 0, e = 1).
-template <int N, int p, int q>
-__device__ __forceinline__ Rot rot_params(Mat<N> &M) {
-    const float hr = M.hr[p][q], hi = M.hi[p][q];
-    const float ha = sqrtf(hr * hr + hi * hi);
-    const float a = M.hr[p][p], b = M.hr[q][q];
-    const bool act = ha > M.skip;
-    const float ihs = act ? 1.0f / ha : 0.f;
-    const float tau = (b - a) * 0.5f * ihs;
-    const float tt = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-    const float t = act ? tt : 0.f;
-    const float c = act ? rsqrtf(fmaf(t, t, 1.0f)) : 1.f;
-    Rot R;
-    R.c = c;
-    R.s = t * c;
-    R.er = act ? hr * ihs : 1.f;
-    R.ei = act ? -hi * ihs : 0.f;
-    M.hr[p][p] = a - t * ha;
-    M.hr[q][q] = b + t * ha;
-    M.hr[p][q] = 0.f;
-    M.hi[p][q] = 0.f;
-    return R;
-}
-
-// Applies a rotation to the rest of H (rows/columns k != p, q) and to V.
-template <int N, int p, int q>
-__device__ __forceinline__ void rot_apply(Mat<N> &M, const Rot &R) {
-    const float c = R.c, s = R.s, er = R.er, ei = R.ei;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        if (k == p || k == q) continue;
-        float xr, xi, yr, yi;
-        hget(M, k, p, xr, xi);
-        hget(M, k, q, yr, yi);
-        const float zr = er * yr - ei * yi, zi = er * yi + ei * yr;   // e^{-i phi} H_kq
-        hset(M, k, p, c * xr - s * zr, c * xi - s * zi);
-        hset(M, k, q, s * xr + c * zr, s * xi + c * zi);
-    }
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const float xr = M.vr[i][p], xi = M.vi[i][p];
-        const float yr = M.vr[i][q], yi = M.vi[i][q];
-        const float zr = er * yr - ei * yi, zi = er * yi + ei * yr;
-        M.vr[i][p] = c * xr - s * zr; M.vi[i][p] = c * xi - s * zi;
-        M.vr[i][q] = s * xr + c * zr; M.vi[i][q] = s * xi + c * zi;
-    }
-}
-
-// Round-robin (tournament) ordering of the N(N-1)/2 pairs: N' - 1 rounds of
-// N'/2 disjoint pairs (N' = N rounded up to even; pairs with the dummy index
-// N' - 1 >= N are left out). The rotations of one round touch disjoint
-// index pairs, so their parameters all come from the matrix at the start of
-// the round and can be computed independently (instruction-level
-// parallelism), then applied one after another.
-template <int N>
-struct RoundRobin {
-    static constexpr int M = (N + 1) & ~1;
-    __host__ __device__ static constexpr int a(int r, int i) { return i == 0 ? r : (r + i) % (M - 1); }
-    __host__ __device__ static constexpr int b(int r, int i) { return i == 0 ? M - 1 : (r - i + M - 1) % (M - 1); }
-    __host__ __device__ static constexpr int lo(int r, int i) { return a(r, i) < b(r, i) ? a(r, i) : b(r, i); }
-    __host__ __device__ static constexpr int hi(int r, int i) { return a(r, i) < b(r, i) ? b(r, i) : a(r, i); }
-};
-
-template <int N, int R, int I>
-struct RoundParams {
-    __device__ __forceinline__ static void run(Mat<N> &M, Rot *rot) {
-        constexpr int p = RoundRobin<N>::lo(R, I), q = RoundRobin<N>::hi(R, I);
-        if constexpr (q < N) rot[I] = rot_params<N, p, q>(M);
-        if constexpr (I + 1 < RoundRobin<N>::M / 2) RoundParams<N, R, I + 1>::run(M, rot);
-    }
-};
-
-template <int N, int R, int I>
-struct RoundApply {
-    __device__ __forceinline__ static void run(Mat<N> &M, const Rot *rot) {
-        constexpr int p = RoundRobin<N>::lo(R, I), q = RoundRobin<N>::hi(R, I);
-        if constexpr (q < N) rot_apply<N, p, q>(M, rot[I]);
-        if constexpr (I + 1 < RoundRobin<N>::M / 2) RoundApply<N, R, I + 1>::run(M, rot);
-    }
-};
-
-template <int N, int R>
-struct Sweep {
-    // rounds R .. N'-2 of one sweep
-    __device__ __forceinline__ static void run(Mat<N> &M) {
-        Rot rot[RoundRobin<N>::M / 2];
-        RoundParams<N, R, 0>::run(M, rot);
-        RoundApply<N, R, 0>::run(M, rot);
-        if constexpr (R + 2 < RoundRobin<N>::M) Sweep<N, R + 1>::run(M);
-    }
-};
-
-template <int N>
-__device__ __forceinline__ float offdiag2(const Mat<N> &M) {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = i + 1; j < N; ++j) s += M.hr[i][j] * M.hr[i][j] + M.hi[i][j] * M.hi[i][j];
-    return s;
-}
-
-template <int N>
-__device__ __forceinline__ void jacobi(Mat<N> &M) {
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) { M.vr[i][j] = (i == j) ? 1.f : 0.f; M.vi[i][j] = 0.f; }
-    if constexpr (N > 1) {
-        float fro = 0.f;
-#pragma unroll
-        for (int i = 0; i < N; ++i) fro += M.hr[i][i] * M.hr[i][i];
-        fro += 2.f * offdiag2(M);
-        // couplings below the FP32 resolution of ||H|| are dropped unrotated; the
-        // 1e-18 floor keeps |h|^2 out of the denormal range, where |h| (and with
-        // it the phase h*/|h| of the rotation) would lose accuracy
-        M.skip = 6e-8f * sqrtf(fro) + 1e-18f;
-        // sweeps until the squared off-diagonal norm is below 1e-14 of
-        // ||H||^2 (FP32 rounding level; convergence is quadratic), at most 12
-        const float tol = 1e-14f * fro + 1e-30f;
-        for (int sweep = 0; sweep < 12; ++sweep) {
-            if (offdiag2(M) <= tol) break;
-            Sweep<N, 0>::run(M);
-        }
-    }
-}
 
 // Lattice vector component reduced to [0, n): staged once per block so that
 // the phase needs only 32-bit products below n^2 <= 2^24.

@@ -1,4 +1,4 @@
-"""GPU batched Jacobi eigensolver (tetra_eig) against LAPACK (FP64 numpy.eigh)."""
+"""GPU batched Hermitian eigensolver (tetra_eig) against LAPACK (FP64 numpy.eigh)."""
 import numpy as np
 import pytest
 
