@@ -92,6 +92,7 @@ template <int N>
 struct Herm {
     float ar[N][N], ai[N][N];   // lower triangle of A used (i >= j)
     float qr[N][N], qi[N][N];   // unitary Q, A = Q T Q^H; then the eigenvectors (columns)
+    float g[N][N];              // real orthogonal G of the QR phase, T = G diag(d) G^T
     float d[N], e[N];           // real tridiagonal T: diagonal, sub-diagonal e[0..N-2]
 };
 
@@ -219,13 +220,19 @@ __device__ __forceinline__ void householder_tridiag(Herm<N> &M) {
     }
 }
 
-// Implicit-shift QR on the real tridiagonal (d, e), rotations accumulated
-// into the columns of Q. Deflation from the bottom: the block [l, m] with
-// m = N-1 .. 1 and l the first row below the last negligible sub-diagonal
-// entry; each step chases the bulge of one Wilkinson-shifted QR step down the
-// block with Givens rotations G = [[c, s], [-s, c]] (T <- G^T T G, Q <- Q G).
+// Implicit-shift QR on the real tridiagonal (d, e), the real rotations
+// accumulated into G (started at the identity; the eigenvectors of H are the
+// columns of Q G, formed once at the end). Deflation from the bottom: the
+// block [l, m] with m = N-1 .. 1 and l the first row below the last
+// negligible sub-diagonal entry; each step chases the bulge of one
+// Wilkinson-shifted QR step down the block with Givens rotations
+// R = [[c, s], [-s, c]] (T <- R^T T R, G <- G R).
 template <int N>
 __device__ __forceinline__ void tridiag_qr(Herm<N> &M) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) M.g[i][j] = (i == j) ? 1.f : 0.f;
     constexpr float kTol = 1.1920929e-07f;   // 2^-23
     float nrm = 0.f;
 #pragma unroll
@@ -269,13 +276,32 @@ __device__ __forceinline__ void tridiag_qr(Herm<N> &M) {
                 }
 #pragma unroll
                 for (int r = 0; r < N; ++r) {
-                    const float xr = M.qr[r][k], xi = M.qi[r][k], yr = M.qr[r][k + 1], yi = M.qi[r][k + 1];
-                    M.qr[r][k] = fmaf(c, xr, -s * yr);
-                    M.qi[r][k] = fmaf(c, xi, -s * yi);
-                    M.qr[r][k + 1] = fmaf(s, xr, c * yr);
-                    M.qi[r][k + 1] = fmaf(s, xi, c * yi);
+                    const float x = M.g[r][k], y = M.g[r][k + 1];
+                    M.g[r][k] = fmaf(c, x, -s * y);
+                    M.g[r][k + 1] = fmaf(s, x, c * y);
                 }
             }
+        }
+    }
+    // eigenvectors: Q <- Q G
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        float vr[N], vi[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                sr = fmaf(M.qr[r][k], M.g[k][n], sr);
+                si = fmaf(M.qi[r][k], M.g[k][n], si);
+            }
+            vr[n] = sr;
+            vi[n] = si;
+        }
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            M.qr[r][n] = vr[n];
+            M.qi[r][n] = vi[n];
         }
     }
 }
