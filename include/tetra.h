@@ -170,7 +170,10 @@ typedef struct {
  * in the tetra layout. A batched Hermitian eigensolver on the GPU (Householder
  * reduction to real tridiagonal form, implicit-shift QR), one k-point per
  * thread; bands ascending, w[n][s] = |V_{s n}|^2 stored in the plan's weight_dtype.
- * Requires plan n_bands == model n_orb <= 8. Halo points are written too. For
+ * Requires plan n_bands == model n_orb <= 8 and plan n_orb <= model n_orb: a
+ * plan with fewer orbitals than the model gets the weights of the model's
+ * first n_orb orbitals (a projection on an orbital subset, as the paper's
+ * five Fe-d orbitals of its eight-orbital model). Halo points are written too. For
  * a slab plan (z_begin, z_end) only the point planes z_begin .. z_end (the
  * corners of its cubes) are written; the rest of eps and w is left as is. */
 tetra_status_t tetra_eig(tetra_plan_t plan, const tetra_model_t *model, float *eps, void *w,

@@ -89,7 +89,14 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
     }
     WT *wo = static_cast<WT *>(A.w) + p * A.w_stride;
     constexpr int VEC = 16 / sizeof(WT);
-    if constexpr ((N * N) % VEC == 0) {
+    if (A.n_orb_out < N) {
+        // projection on the first n_orb_out orbitals only: w[n][s], s < n_orb_out
+#pragma unroll
+        for (int n = 0; n < N; ++n)
+#pragma unroll
+            for (int s = 0; s < N; ++s)
+                if (s < A.n_orb_out) wo[n * A.n_orb_out + s] = from_f32<WT>(W[n][s]);
+    } else if constexpr ((N * N) % VEC == 0) {
 #pragma unroll
         for (int v = 0; v < N * N / VEC; ++v) {
             uint4 q;
@@ -123,7 +130,7 @@ cudaError_t launch_n(const Plan &P, const EigArgs &A, cudaStream_t stream) {
 tetra_status_t launch_eig(const Plan &P, const tetra_model_t *m, float *eps, void *w,
                           cudaStream_t stream) {
     if (!m || !m->params || (m->n_R > 0 && !m->R) || !eps || !w) return TETRA_EINVAL;
-    if (m->n_orb < 1 || m->n_orb > 8 || m->n_orb != P.d.n_bands || m->n_orb != P.d.n_orb)
+    if (m->n_orb < 1 || m->n_orb > 8 || m->n_orb != P.d.n_bands || P.d.n_orb > m->n_orb)
         return TETRA_EUNSUPPORTED;
     if (m->n_R < 0 || m->n_R > kMaxR) return TETRA_EINVAL;
     EigArgs A;

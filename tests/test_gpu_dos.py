@@ -289,3 +289,27 @@ def test_slabs_of_one_model_on_separate_plans(T):
     E_h, W_h = from_layout(eps.cpu().numpy(), w.cpu().numpy(), *n, 8, 8)
     r = oracle.dos(E_h, W_h, *n, om.cpu().numpy().astype(np.float64), nthreads=NTHREADS)
     assert_parity(total, r)
+
+
+def test_paper_shape_five_projected_orbitals(T):
+    """The paper's benchmark shape (Sec. IV: 60 x 60 x 10 k-grid, 8 bands, the
+    DOS projected on 5 of the 8 orbitals, 1024 energies), on the synthetic
+    8-orbital model: GPU eigensolver writing the first 5 orbitals' weights,
+    then the DOS, against the oracle on the same FP32 eigen-data."""
+    from helpers import model_arrays
+
+    n = (60, 60, 10)
+    model = tbgen.tb_model(21, n_orb=8)
+    p, R = model_arrays(model)
+    dev = torch.device("cuda")
+    plan = T.Plan(*n, 8, 5, 1024)
+    eps, w = plan.eig(torch.from_numpy(p).to(dev), torch.from_numpy(R).to(dev))
+    lo, hi = float(eps[..., :8].min()) - 0.1, float(eps[..., :8].max()) + 0.1
+    om = torch.from_numpy(tbgen.uniform_grid(lo, hi, 1024)).to(dev)
+    g = plan.dos(eps, w, om).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    assert plan.status() == T.TETRA_OK
+    E_h, W_h = from_layout(eps.cpu().numpy(), w.cpu().numpy(), *n, 8, 5)
+    r = oracle.dos(E_h, W_h, *n, om.cpu().numpy().astype(np.float64), nthreads=NTHREADS)
+    assert g.shape == (5, 1024)
+    assert_parity(g, r)

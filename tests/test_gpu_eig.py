@@ -112,3 +112,21 @@ def test_slab_plan_writes_only_its_planes(T):
     assert np.array_equal(Ws[2:6, ..., :64], W[2:6, ..., :64])   # w_stride 68: 4 padding entries
     assert np.isnan(Es[:2]).all() and np.isnan(Es[6:]).all()
     assert np.isnan(Ws[:2]).all() and np.isnan(Ws[6:]).all()
+
+
+def test_orbital_subset_weights(T):
+    """A plan with fewer orbitals than the model stores the weights of the
+    model's first orbitals, bit for bit as the full projection does."""
+    n = (5, 6, 4)
+    model = tbgen.tb_model(12, n_orb=8)
+    _, E8, W8 = gpu_eig(T, model, n)
+    plan = T.Plan(*n, 8, 5, 16)
+    p, R = model_arrays(model)
+    dev = torch.device("cuda")
+    eps, w = plan.eig(torch.from_numpy(p).to(dev), torch.from_numpy(R).to(dev))
+    torch.cuda.synchronize()
+    E5, W5 = eps.cpu().numpy(), w.cpu().numpy()
+    assert np.array_equal(E5, E8)
+    w8 = W8[..., :64].reshape(W8.shape[:3] + (8, 8))
+    w5 = W5[..., :40].reshape(W5.shape[:3] + (8, 5))
+    assert np.array_equal(w5, w8[..., :5])
