@@ -132,7 +132,9 @@ def dos(eps, w, n1, n2, n3, energies, mode="point", edges_hi=None, z_range=None,
     """Orbital-resolved DOS, Eqs. (8)-(9).
 
     eps (nk, nb), w (nk, nb, norb) in the natural layout. Point mode:
-    ``energies`` is any list of E values. Bin mode: either ``energies`` holds
+    ``energies`` is any list of E values. Integrated mode: the orbital
+    occupation n_s(E) = sum_{tetra,n} sum_l b_{n,l,s} w_l(E) (Eq. (2) with the
+    step function as occupation) at each E of ``energies``. Bin mode: either ``energies`` holds
     nbins+1 ascending edges, or ``energies``/``edges_hi`` hold the lower and
     upper edge of each bin. Returns (norb, npts).
     """
@@ -147,6 +149,10 @@ def dos(eps, w, n1, n2, n3, energies, mode="point", edges_hi=None, z_range=None,
         ea = _c64(energies)
         eb = ea
         m = 0
+    elif mode == "integrated":
+        ea = _c64(energies)
+        eb = ea
+        m = 2
     elif mode == "bin":
         if edges_hi is None:
             e = _c64(energies)
@@ -246,3 +252,30 @@ def eig_backward(model: dict, n1: int, n2: int, n3: int, geps, gw) -> np.ndarray
         g_re.append(np.real(Zs))
         g_im.append(-np.imag(Zs))
     return np.concatenate([g_on, np.array(g_re).ravel(), np.array(g_im).ravel()])
+
+
+# ---------------------------------------------------------------- Fermi level
+def fermi_level(eps, n1, n2, n3, n_electrons, tol=1e-12, nthreads: int = 1):
+    """Energy E_F at which the integrated count of states per spin,
+    N(E) = sum_{tetra,n} sum_l w_l(E) (Eq. (2), Sec. II.C weights, every
+    orbital weight 1), equals n_electrons; plain bisection in FP64 on
+    [min eps, max eps]. N is continuous and non-decreasing, so bisection
+    converges to the lowest such energy within tol."""
+    eps = _c64(eps)
+    nk, nb = eps.shape
+    ones = np.ones((nk, nb, 1))
+    lo, hi = float(eps.min()), float(eps.max())
+    if not (0.0 <= n_electrons <= nb):
+        raise ValueError("n_electrons must lie in [0, n_bands]")
+
+    def count(E):
+        return float(dos(eps, ones, n1, n2, n3, np.array([E]), mode="integrated",
+                         nthreads=nthreads)[0, 0])
+
+    while hi - lo > tol * max(1.0, abs(lo), abs(hi)):
+        mid = 0.5 * (lo + hi)
+        if count(mid) < n_electrons:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)

@@ -223,6 +223,10 @@ static void sort4(double e[4], int pos[4]) {
  * mode 0 (point): dos[s*npts+i] = sum_{tetra,n} sum_l b_{n,l,s} dw_l/dE at E = ea[i].
  * mode 1 (bin):   dos[s*npts+i] = sum_{tetra,n} sum_l b_{n,l,s}
  *                                 [w_l(eb[i]) - w_l(ea[i])] / (eb[i] - ea[i]).
+ * mode 2 (integrated): dos[s*npts+i] = sum_{tetra,n} sum_l b_{n,l,s} w_l(ea[i]),
+ *                 the orbital occupation up to E (Eq. (2) with the step
+ *                 function as occupation, evaluated by the corner weights of
+ *                 Sec. II.C).
  * The energies ea/eb may be any list (a sample of a grid is fine).
  * Cubes with z in [z0, z1) only (the whole grid for z0=0, z1=n3).
  * nthreads > 1 splits the cube planes into contiguous blocks and adds the
@@ -272,6 +276,9 @@ int oracle_dos_range(int n1, int n2, int n3, int nb, int norb, const double *eps
                                 if (mode == 0) {
                                     oracle_corner_weights(e, ea[i], f, w, dw);
                                     for (q = 0; q < 4; ++q) c[q] = dw[q];
+                                } else if (mode == 2) {
+                                    oracle_corner_weights(e, ea[i], f, w, dw);
+                                    for (q = 0; q < 4; ++q) c[q] = w[q];
                                 } else {
                                     oracle_corner_weights(e, ea[i], f, w, dw);
                                     oracle_corner_weights(e, eb[i], f, w2, dw2);

@@ -445,3 +445,68 @@ def test_eig_backward_matches_finite_difference_of_fp64_chain():
         pm = p0.copy(); pm[i] -= h
         fd = (loss(pp) - loss(pm)) / (2 * h)
         assert abs(fd - grad[i]) < 2e-5 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+# ---------------------------------------------------------------- integrated occupation n_s(E)
+def test_integrated_occupation_limits():
+    """Below every band n_s(E) = 0; above every band each k-point is a corner
+    of 24 tetrahedra of weight V_T/(4 V_G) = 1/(24 N_k), so n_s is the plain
+    k-average of sum_n b_sn (computed here directly from the weights)."""
+    n1, n2, n3, eps, w = small_problem(seed=5, n=(3, 4, 2), nb=3, norb=2)
+    E = np.array([eps.min() - 1.0, eps.max() + 1.0])
+    n = oracle.dos(eps, w, n1, n2, n3, E, mode="integrated")
+    np.testing.assert_array_equal(n[:, 0], 0.0)
+    np.testing.assert_allclose(n[:, 1], w.sum(axis=1).mean(axis=0), rtol=1e-12)
+
+
+def test_integrated_occupation_monte_carlo_of_linear_interpolant():
+    """n_s(E) equals the integral of the linearly interpolated weight b_s over
+    the region where the linearly interpolated band lies below E (uniform
+    samples in every cube, tetrahedron located from Table I)."""
+    n1, n2, n3, eps, w = small_problem(seed=12, n=(2, 2, 2), nb=1, norb=2)
+    rng = np.random.default_rng(7)
+    E = np.linspace(eps.min() + 0.1, eps.max() - 0.1, 7)
+    acc = np.zeros((2, len(E)))
+    tets = [np.array([corner_offset(c) for c in tet]) for tet in TABLE_I]
+    inv = [np.linalg.inv((P[:3] - P[3]).T) for P in tets]
+    ns = 300_000
+    for z in range(n3):
+        for y in range(n2):
+            for x in range(n1):
+                pts = rng.uniform(0, 1, (ns, 3))
+                for P, Ti, tet in zip(tets, inv, TABLE_I):
+                    lam = (Ti @ (pts - P[3]).T).T
+                    lam = np.concatenate([lam, 1 - lam.sum(1, keepdims=True)], 1)
+                    L = lam[np.all(lam >= 0, axis=1)]
+                    ks = []
+                    for c in tet:
+                        o = corner_offset(c).astype(int)
+                        ks.append(((x + o[0]) % n1) + n1 * (((y + o[1]) % n2) + n2 * ((z + o[2]) % n3)))
+                    ev = L @ eps[ks, 0]
+                    for s in range(2):
+                        bv = L @ w[ks, 0, s]
+                        acc[s] += [(bv * (ev < e)).sum() for e in E]
+    acc /= ns * n1 * n2 * n3
+    n = oracle.dos(eps, w, n1, n2, n3, E, mode="integrated")
+    assert np.max(np.abs(acc - n)) < 0.01 * np.max(n)
+
+
+def test_simple_cubic_half_filling():
+    """eps(k + (pi,pi,pi)) = -eps(k) on an even grid maps the states below E
+    onto those above -E, so N(0) = 1/2 exactly and the Fermi level of half
+    filling is 0."""
+    n = 8
+    eps = sc_eps(n)
+    N = oracle.dos(eps, np.ones((n ** 3, 1, 1)), n, n, n, np.array([0.0]), mode="integrated")
+    assert abs(N[0, 0] - 0.5) < 1e-12
+    assert abs(oracle.fermi_level(eps, n, n, n, 0.5)) < 1e-9
+
+
+def test_fermi_level_is_the_root_of_the_count():
+    n1, n2, n3, eps, w = small_problem(seed=8, n=(4, 3, 3), nb=3, norb=2)
+    for ne in (0.4, 1.0, 2.3):
+        ef = oracle.fermi_level(eps, n1, n2, n3, ne)
+        N = oracle.dos(eps, np.ones(w.shape[:2] + (1,)), n1, n2, n3, np.array([ef - 1e-6, ef, ef + 1e-6]),
+                       mode="integrated")[0]
+        assert N[0] <= ne + 1e-9 and N[2] >= ne - 1e-9
+        assert abs(N[1] - ne) < 1e-6
