@@ -55,7 +55,7 @@ typedef enum {
     TETRA_ERANGE = 6         /* a contribution exceeded the fixed-point range     */
 } tetra_status_t;
 
-enum { TETRA_POINT = 0, TETRA_BIN = 1 };
+enum { TETRA_POINT = 0, TETRA_BIN = 1, TETRA_INTEGRATED = 2 };
 enum { TETRA_F32 = 0, TETRA_F16 = 1, TETRA_BF16 = 2 };
 
 /* Problem description of one DOS evaluation. */
@@ -63,9 +63,10 @@ typedef struct {
     int n1, n2, n3;     /* k-grid size, each >= 1                                   */
     int n_bands;        /* bands per k-point, 1..64                                 */
     int n_orb;          /* orbitals, 1..16 (Sec. III.B: up to 16 orbitals)          */
-    int n_omega;        /* energies (TETRA_POINT) or bins (TETRA_BIN), >= 1         */
+    int n_omega;        /* energies (TETRA_POINT, TETRA_INTEGRATED) or bins (TETRA_BIN), >= 1 */
     int mode;           /* TETRA_POINT: rho_s(E) at energies, Eq. (9);
-                           TETRA_BIN: bin averages of rho_s over consecutive edges */
+                           TETRA_BIN: bin averages of rho_s over consecutive edges;
+                           TETRA_INTEGRATED: occupation n_s(E) up to each energy */
     int weight_dtype;   /* storage type of w: TETRA_F32, TETRA_F16, TETRA_BF16      */
     int z_begin, z_end; /* cube planes [z_begin, z_end) to integrate (a k-slab, for
                            splitting one grid over several calls or devices);
@@ -99,7 +100,7 @@ size_t tetra_workspace_bytes(tetra_plan_t plan);
 
 /* Orbital-resolved DOS by the linear tetrahedron method (Sec. II.C, Eqs. (8)-(9)).
  *   eps, w : band energies and orbital weights in the tetra layout.
- *   omega  : TETRA_POINT: n_omega ascending energies E_i.
+ *   omega  : TETRA_POINT, TETRA_INTEGRATED: n_omega ascending energies E_i.
  *            TETRA_BIN:   n_omega + 1 ascending bin edges.
  *            Any ascending grid is correct; equidistant grids (Sec. IV.A) are
  *            fastest.
@@ -107,8 +108,15 @@ size_t tetra_workspace_bytes(tetra_plan_t plan);
  *            TETRA_POINT: dos[s][i] = sum_{T,n} sum_l b_{n,l,s} dw_l/dE (E_i).
  *            TETRA_BIN:   dos[s][i] = sum_{T,n} sum_l b_{n,l,s}
  *                           [w_l(e_{i+1}) - w_l(e_i)] / (e_{i+1} - e_i).
+ *            TETRA_INTEGRATED: dos[s][i] = sum_{T,n} sum_l b_{n,l,s} w_l(E_i),
+ *                           the occupation of orbital s per spin up to E_i
+ *                           (Eq. (2) with the step function as occupation;
+ *                           not in the paper, which integrates the DOS only).
+ *                           The whole energy grid must fit one shared-memory
+ *                           tile (about 2000 energies for 8 orbitals; the plan
+ *                           returns TETRA_EUNSUPPORTED otherwise).
  *            Normalised per spin and orbital: with unitary weights the bin
- *            DOS of each orbital integrates to 1.
+ *            DOS of each orbital integrates to 1, and n_s(E) rises from 0 to 1.
  *   ws     : device workspace of at least tetra_workspace_bytes(plan) bytes,
  *            16-byte aligned; contents on entry are ignored.
  * Returns TETRA_EINVAL for null/misaligned pointers or ws_bytes too small. */
@@ -125,8 +133,9 @@ tetra_status_t tetra_dos(tetra_plan_t plan, const float *eps, const void *w,
  *   Scratch: a static device array of 32 MiB inside libtetra (held on every
  *   GPU that loads the library until the process exits). The call allocates
  *   nothing. If the plan's per-CTA partial sums do not fit, fewer persistent
- *   CTAs are used (same result, bit for bit); if n_orb * n_omega * 8 bytes plus
- *   256 bytes exceeds 32 MiB even with one CTA, returns TETRA_ENOMEM.
+ *   CTAs are used (same result, bit for bit); if they do not fit even with one
+ *   CTA (n_orb * n_omega * 8 bytes, twice that in TETRA_INTEGRATED mode, plus
+ *   256 bytes, above 32 MiB), returns TETRA_ENOMEM.
  *   Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
  *   before any stream capture.
@@ -241,6 +250,29 @@ tetra_status_t tetra_batch_info(tetra_batch_plan_t plan, int *box, int *grid, in
 tetra_status_t tetra_dos_batched(tetra_batch_plan_t plan, const float *const *eps, const void *const *w,
                                  const float *const *omega, float *const *dos, void *ws,
                                  size_t ws_bytes, cudaStream_t stream);
+
+/* Fermi level of the plan's bands: the energy E_F at which the occupation
+ * summed over the plan's orbitals, N(E) = sum_s n_s(E) (TETRA_INTEGRATED mode
+ * of tetra_dos: Eq. (2) with the step function as occupation, Sec. II.C
+ * corner weights), equals n_electrons per spin. With unitary weights of all
+ * orbitals (tetra_eig with plan n_orb = n_bands) N counts the states below E,
+ * from 0 to n_bands. Not in the paper (which evaluates the DOS only).
+ *   eps, w : as for tetra_dos, for any plan mode (the plan's grid, bands,
+ *            orbitals and weight dtype are used).
+ *   n_electrons : target count per spin, in [0, N(max eps)].
+ *   ef     : host float, the result.
+ *   ws     : device workspace of at least tetra_fermi_workspace_bytes(plan)
+ *            bytes, 16-byte aligned.
+ * Method: the band minimum and maximum bracket E_F; each round evaluates N at
+ * 64 equidistant energies of the bracket in one TETRA_INTEGRATED launch and
+ * keeps the sub-interval where N crosses n_electrons, until the bracket is at
+ * the FP32 resolution of the energies (about six rounds). Synchronises
+ * `stream` once per round. Returns TETRA_EINVAL for null/misaligned pointers
+ * or n_electrons outside [0, N(max eps)], TETRA_ENOMEM if ws_bytes is too
+ * small, TETRA_EUNSUPPORTED for a slab plan (the count needs the whole grid). */
+size_t tetra_fermi_workspace_bytes(tetra_plan_t plan);
+tetra_status_t tetra_fermi_level(tetra_plan_t plan, const float *eps, const void *w, double n_electrons,
+                                 float *ef, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Device-side status recorded in a workspace by the last call that used it
  * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. */

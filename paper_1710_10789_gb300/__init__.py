@@ -19,21 +19,21 @@ import threading
 from . import _build
 
 __all__ = [
-    "TETRA_OK", "TETRA_POINT", "TETRA_BIN", "TETRA_F32", "TETRA_F16", "TETRA_BF16",
+    "TETRA_OK", "TETRA_POINT", "TETRA_BIN", "TETRA_INTEGRATED", "TETRA_F32", "TETRA_F16", "TETRA_BF16",
     "TetraError", "TetraDesc", "TetraLayout", "TetraModel", "build", "lib", "lib_path",
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc", "Plan",
     "EXPORTED_SYMBOLS", "TetraTune", "tetra_plan_batched", "tetra_batch_plan_destroy",
     "tetra_batch_layout", "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
-    "BatchPlan", "TETRA_MAX_BATCH",
+    "BatchPlan", "TETRA_MAX_BATCH", "tetra_fermi_workspace_bytes", "tetra_fermi_level",
 ]
 
 TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
-TETRA_POINT, TETRA_BIN = 0, 1
+TETRA_POINT, TETRA_BIN, TETRA_INTEGRATED = 0, 1, 2
 TETRA_F32, TETRA_F16, TETRA_BF16 = 0, 1, 2
 _DTYPES = {"f32": TETRA_F32, "f16": TETRA_F16, "bf16": TETRA_BF16}
-_MODES = {"point": TETRA_POINT, "bin": TETRA_BIN}
+_MODES = {"point": TETRA_POINT, "bin": TETRA_BIN, "integrated": TETRA_INTEGRATED}
 
 #: Every extern "C" symbol declared in include/tetra.h.
 EXPORTED_SYMBOLS = (
@@ -42,6 +42,7 @@ EXPORTED_SYMBOLS = (
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc",
     "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
     "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
+    "tetra_fermi_workspace_bytes", "tetra_fermi_level",
 )
 TETRA_MAX_BATCH = 64
 
@@ -121,6 +122,10 @@ def lib():
             L.tetra_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
             L.tetra_dos_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                             ctypes.POINTER(vp), ctypes.POINTER(vp), vp, sz, vp]
+            L.tetra_fermi_workspace_bytes.argtypes = [vp]
+            L.tetra_fermi_workspace_bytes.restype = sz
+            L.tetra_fermi_level.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
+                                            vp, sz, vp]
             L.tetra_strerror.argtypes = [i]
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
@@ -129,7 +134,7 @@ def lib():
                          "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
                          "tetra_workspace_status", "tetra_plan_batched",
                          "tetra_batch_plan_destroy", "tetra_batch_layout", "tetra_batch_info",
-                         "tetra_dos_batched"):
+                         "tetra_dos_batched", "tetra_fermi_level"):
                 getattr(L, name).restype = i
             _LIB = L
     return _LIB
@@ -163,6 +168,14 @@ def tetra_workspace_bytes(plan: int) -> int:
 
 def tetra_dos(plan, eps, w, omega, dos, ws, ws_bytes, stream) -> int:
     return lib().tetra_dos(plan, eps, w, omega, dos, ws, ws_bytes, stream)
+
+
+def tetra_fermi_workspace_bytes(plan) -> int:
+    return lib().tetra_fermi_workspace_bytes(plan)
+
+
+def tetra_fermi_level(plan, eps, w, n_electrons, ef, ws, ws_bytes, stream) -> int:
+    return lib().tetra_fermi_level(plan, eps, w, float(n_electrons), ef, ws, ws_bytes, stream)
 
 
 def tetra_dos_noalloc(plan, eps, w, omega, dos, stream) -> int:
@@ -325,6 +338,19 @@ class Plan:
                                   _ptr(grad_dos.contiguous()), _ptr(grad_eps), _ptr(grad_w),
                                   _ptr(ws), ws.numel(), _stream_handle(stream)), "tetra_dos_backward")
         return grad_eps, grad_w
+
+    def fermi_level(self, eps, w, n_electrons, stream=None) -> float:
+        """E_F with sum over the plan's orbitals of n_s(E_F) = n_electrons per spin
+        (tetra_fermi_level)."""
+        torch = _torch()
+        nbytes = tetra_fermi_workspace_bytes(self.handle)
+        if nbytes == 0:
+            raise TetraError(TETRA_EUNSUPPORTED, "tetra_fermi_workspace_bytes")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=eps.device)
+        ef = ctypes.c_float(0.0)
+        _check(tetra_fermi_level(self.handle, _ptr(eps), _ptr(w), n_electrons, ctypes.byref(ef), _ptr(ws),
+                                 ws.numel(), _stream_handle(stream)), "tetra_fermi_level")
+        return float(ef.value)
 
     def _model(self, params, R):
         n_orb = self.desc.n_bands

@@ -101,10 +101,14 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     const size_t fixed = 2 * stage + 6 * (size_t)P.items_per_box + 16 + 2 * 256 * 4 + 32 + 1024 + 512 + 128 +
                          4 * (size_t)P.tile_stride;
     // per energy: int tile row, cached energy, 1/width (bin mode), block bound share
-    const size_t per_w = 4 * (size_t)(P.tile_stride + 1 + (d.mode == TETRA_BIN ? 1 : 0)) + 1;
+    // (integrated mode: plus a row of per-orbital step sums)
+    const size_t per_w = 4 * (size_t)(P.tile_stride + 1 + (d.mode == TETRA_BIN ? 1 : 0) +
+                                      (d.mode == TETRA_INTEGRATED ? P.tile_stride - 1 : 0)) + 1;
     if (fixed + per_w * 64 > P.smem_optin) return TETRA_EUNSUPPORTED;
     int cw = (int)std::min<size_t>((P.smem_optin - fixed - 8) / per_w, (size_t)d.n_omega);
     P.n_chunks = (d.n_omega + cw - 1) / cw;
+    // the integrated mode's steps reach every later energy: one chunk only
+    if (d.mode == TETRA_INTEGRATED && P.n_chunks != 1) return TETRA_EUNSUPPORTED;
     P.chunk_w = (d.n_omega + P.n_chunks - 1) / P.n_chunks;
     P.smem_bytes = fixed + per_w * P.chunk_w + 8;
     P.threads = pairs ? 384 : 512;
@@ -121,6 +125,10 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
         const double need = 1e5 * d.n_omega / std::sqrt(items);
         int F = (int)std::ceil(std::log2(std::max(need, 1.0)));
         F = std::max(17, std::min(28, F));
+        // integrated occupation: a tetrahedron's full weight V_T/V_G is 2^18
+        // units (per-item rounding below 2e-6 of it, and a box's items stay
+        // under the int32 tile's per-item cap)
+        if (d.mode == TETRA_INTEGRATED) F = 18;
         P.fixed_bits = env_int("TETRA_FIXED_BITS", F);
     }
     // tile blocks are flushed at a bound of 2^30 (a lower value, for tests of
@@ -135,7 +143,7 @@ tetra_status_t plan_init(Plan &P, const tetra_desc_t &d, int device, const int b
         return TETRA_EINVAL;
     if (d.n_bands < 1 || d.n_bands > 64 || d.n_orb < 1 || d.n_orb > 16 || d.n_omega < 1)
         return TETRA_EINVAL;
-    if (d.mode != TETRA_POINT && d.mode != TETRA_BIN) return TETRA_EINVAL;
+    if (d.mode != TETRA_POINT && d.mode != TETRA_BIN && d.mode != TETRA_INTEGRATED) return TETRA_EINVAL;
     if (d.weight_dtype != TETRA_F32 && d.weight_dtype != TETRA_F16 && d.weight_dtype != TETRA_BF16)
         return TETRA_EINVAL;
     int z0 = d.z_begin, z1 = d.z_end;
@@ -263,6 +271,7 @@ tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *
     *plan = nullptr;
     if (n_models < 1 || n_models > tetra::kMaxBatch) return TETRA_EINVAL;
     const tetra_desc_t &d0 = descs[0];
+    if (d0.mode == TETRA_INTEGRATED) return TETRA_EUNSUPPORTED;   // single-model plans only
     for (int m = 1; m < n_models; ++m) {
         const tetra_desc_t &d = descs[m];
         if (d.n_bands != d0.n_bands || d.n_orb != d0.n_orb || d.mode != d0.mode ||

@@ -115,15 +115,21 @@ struct FwdArgs {
     int fast_cap;
     unsigned flush_at;   // a 64-energy block is flushed once its bound reaches this
     long long *G;        // int64 partials, [slot][n_orb][chunk_w]
+    long long *Gs;       // integrated mode: int64 partial step sums, [slot][n_orb][chunk_w]
     int *status;
     int *queue;          // batched: next unclaimed (model, box) work item
 };
 
-// Fixed-point unit, identical in every kernel that uses it.
+// Fixed-point unit, identical in every kernel that uses it. The DOS modes
+// scale with the mean energy spacing (their values are per energy); the
+// integrated occupation is dimensionless, so its unit does not depend on the
+// grid (a narrow grid, as in a Fermi-level search, keeps full resolution).
 __device__ __forceinline__ double fixed_unit(const float *omega, int n_omega, int mode, double vtvg,
                                              int bits) {
     double de;
-    if (mode == TETRA_POINT)
+    if (mode == TETRA_INTEGRATED)
+        de = 1.0;
+    else if (mode != TETRA_BIN)
         de = n_omega > 1 ? ((double)omega[n_omega - 1] - (double)omega[0]) / (n_omega - 1) : 1.0;
     else
         de = ((double)omega[n_omega] - (double)omega[0]) / n_omega;
@@ -337,7 +343,7 @@ __device__ __forceinline__ void item_window(float e1, float e4, const float *om,
                                             float om0, float inv_de, int n_omega, int &lo, int &hi) {
     const float flo = fminf(fmaxf((e1 - om0) * inv_de, -2.f), (float)n_omega + 2.f);
     const float fhi = fminf(fmaxf((e4 - om0) * inv_de, -2.f), (float)n_omega + 2.f);
-    if (MODE == TETRA_POINT) {
+    if (MODE != TETRA_BIN) {
         lo = min(max((int)floorf(flo) + 1, w0), w0 + wc);
         hi = max(min((int)ceilf(fhi) - 1, w0 + wc - 1), w0 - 1);
         while (lo > w0 && om[lo - 1 - w0] > e1) --lo;
@@ -411,7 +417,10 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     // shared memory carve-up
     unsigned char *stage[2] = {smem, smem + A.stage_bytes};
     int *tile = reinterpret_cast<int *>(smem + 2 * A.stage_bytes);   // [chunk_w + 1][TS]
-    float *om = reinterpret_cast<float *>(tile + TS * (A.chunk_w + 1));   // energies / edges
+    // integrated mode: per-orbital sums of the saturated weights of the items
+    // whose E4 lies between energy j-1 and j, [chunk_w][NORB] (plain integers)
+    int *stile = tile + TS * (A.chunk_w + 1);
+    float *om = reinterpret_cast<float *>(stile + (MODE == TETRA_INTEGRATED ? NORB * A.chunk_w : 0));
     float *iw = om + A.chunk_w + 1;                                   // 1/bin width (bin mode)
     unsigned *blk_bound = reinterpret_cast<unsigned *>(iw + (MODE == TETRA_BIN ? A.chunk_w : 0));
     const int n_blk = (A.chunk_w + 63) >> 6;
@@ -557,6 +566,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         return (int)((unsigned)tile[j * TS + s] - n_add * (unsigned)kMagicBits);
     };
     // moves the int32 tile of the current model into its int64 partial slot
+    long long *Gsc = A.Gs;
     auto flush_tile = [&]() {
         counts_from_diffs();
         for (int i = tid; i < A.n_orb * wc; i += blockDim.x) {
@@ -565,6 +575,12 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             if (v)
                 atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j),
                           static_cast<unsigned long long>(static_cast<long long>(v)));
+            if (MODE == TETRA_INTEGRATED) {
+                const int sv = stile[j * NORB + s];
+                if (sv)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(Gsc + (long)s * A.chunk_w + j),
+                              static_cast<unsigned long long>(static_cast<long long>(sv)));
+            }
         }
     };
 
@@ -583,9 +599,12 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             // per model for a batch (CTAs flush into it with integer atomics)
             const long slot = (MAXM == 1) ? (long)chunk * gridDim.x + blockIdx.x : (long)mi;
             Gc = A.G + slot * (long)A.n_orb * A.chunk_w;
+            if (MODE == TETRA_INTEGRATED) Gsc = A.Gs + slot * (long)A.n_orb * A.chunk_w;
             for (int i = tid; i < TS * (A.chunk_w + 1); i += blockDim.x) tile[i] = 0;
+            if (MODE == TETRA_INTEGRATED)
+                for (int i = tid; i < NORB * A.chunk_w; i += blockDim.x) stile[i] = 0;
             for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
-            const int n_om = (MODE == TETRA_POINT) ? wc : wc + 1;
+            const int n_om = (MODE != TETRA_BIN) ? wc : wc + 1;
             for (int i = tid; i < n_om; i += blockDim.x) om[i] = M.omega[w0 + i];
             __syncthreads();
             if (MODE == TETRA_BIN)
@@ -593,8 +612,8 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             u = fixed_unit(M.omega, M.n_omega, MODE, M.vtvg, M.fixed_bits);
             fq = (float)(0.25 * M.vtvg / u);   // V_T/(4 V_G) in fixed-point units
             om0 = M.omega[0];
-            const float omN = (MODE == TETRA_POINT) ? M.omega[M.n_omega - 1] : M.omega[M.n_omega];
-            inv_de = (MODE == TETRA_POINT) ? (M.n_omega > 1 ? (float)(M.n_omega - 1) / (omN - om0) : 0.f)
+            const float omN = (MODE != TETRA_BIN) ? M.omega[M.n_omega - 1] : M.omega[M.n_omega];
+            inv_de = (MODE != TETRA_BIN) ? (M.n_omega > 1 ? (float)(M.n_omega - 1) / (omN - om0) : 0.f)
                                            : (float)M.n_omega / (omN - om0);
             if (MODE == TETRA_BIN) {
                 // the narrowest bin of the whole grid bounds every bin contribution
@@ -653,7 +672,10 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         // adds them, so the grouping cannot change the result.
         for (int base = warp * 32; base < A.items_per_box; base += nwarp * 32) {
             const int it = base + lane;
-            int K = 0, lo = 0;
+            // integrated mode: an item also counts when only its step (the first
+            // energy at or above E4) lies in the chunk; items off the grid get
+            // lo = w0 + wc, which makes them inactive
+            int K = 0, lo = (MODE == TETRA_INTEGRATED) ? w0 + wc : 0;
             if (it < A.items_per_box) {
                 constexpr bool PAIRS = Cfg<MODE, NORB>::pairs;
                 constexpr int UPC = Cfg<MODE, NORB>::units_per_cube;
@@ -681,7 +703,8 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 s_lo[it] = (short)(lo - w0);
                 s_K[it] = (unsigned short)K;
             }
-            if (K > 0) atomicAdd(&khist[min(K, kKBins - 1)], 1);
+            const bool act = K > 0 || (MODE == TETRA_INTEGRATED && lo + K < w0 + wc);
+            if (act) atomicAdd(&khist[min(K, kKBins - 1)], 1);
         }
         __syncthreads();
         // Items ranked by window length K: an exclusive scan of the K histogram
@@ -710,7 +733,9 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         for (int base = warp * 32; base < A.items_per_box; base += nwarp * 32) {
             const int it = base + lane;
             const int K = it < A.items_per_box ? (int)s_K[it] : 0;
-            if (K > 0) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
+            const bool act = it < A.items_per_box &&
+                             (K > 0 || (MODE == TETRA_INTEGRATED && s_lo[it] + K < wc));
+            if (act) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
         }
         __syncthreads();
         const int n_active = s_active;
@@ -843,20 +868,71 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             // per-item bound on every |contribution|, in fixed-point units (the
             // tetrahedron DOS is at most 3/E41 of V_T/V_G; a bin average at most
             // its weight step over the narrowest bin)
+            // (integrated mode: every corner weight is at most V_T/(4 V_G))
             float qmax = (MODE == TETRA_POINT) ? bmax * 4.f * fq * 3.1f * safe_rcp(e[3] - e[0])
-                                               : bmax * 4.f * fq * max_iw * 1.01f;
-            if (!(e[3] > e[0])) qmax = 3.0e38f;
+                         : (MODE == TETRA_BIN) ? bmax * 4.f * fq * max_iw * 1.01f
+                                               : bmax * 4.f * fq * 1.01f;
+            if (!(e[3] > e[0]) && MODE != TETRA_INTEGRATED) qmax = 3.0e38f;
             const bool fast = qmax < (float)A.fast_cap;
             const float dith = item_dither((gcube * 6u + (uint32_t)t) * (uint32_t)A.nb + (uint32_t)n);
             if (!valid) continue;
+            // integrated mode: the first energy at or above E4, where the item's
+            // saturated weights enter the step tile (none if beyond the grid)
+            const int hs = hi + 1;
+            const bool step = MODE == TETRA_INTEGRATED && hs < w0 + wc;
             // Bookkeeping of the tile: every entry of blocks lo/64 .. hi/64 may
             // receive at most qmax from this item, and rows lo .. hi each receive
             // one add per orbital.
             if (fast) {
                 const unsigned qbnd = (unsigned)qmax + 2u;
-                for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
-                atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
-                atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
+                if (hi >= lo) {
+                    for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
+                    atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
+                    atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
+                }
+                if (step) atomicAdd(&blk_bound[(hs - w0) >> 6], qbnd);
+            }
+            if constexpr (MODE == TETRA_INTEGRATED) {
+                Tet T;
+                tet_setup(T, e[0], e[1], e[2], e[3], fq);
+                float bsum[NORB];   // saturated contribution: fq sum_l b_{l,s}
+#pragma unroll
+                for (int s = 0; s < NORB; ++s) bsum[s] = fq * ((b[0][s] + b[1][s]) + (b[2][s] + b[3][s]));
+                if (fast) {
+                    const int K = hi - lo + 1;
+                    int i = lo + ((lane * max(K, 1)) >> 5);
+                    for (int j = 0; j < K; ++j) {
+                        float wl[4];
+                        tet_weights(T, om[i - w0], wl);
+                        int *col = tile + (i - w0) * TS;
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            float acc = fmaf(b[0][s], wl[0], dith);
+                            acc = fmaf(b[1][s], wl[1], acc);
+                            acc = fmaf(b[2][s], wl[2], acc);
+                            acc = fmaf(b[3][s], wl[3], acc);
+                            atomicAdd(col + s, __float_as_int(acc + kMagic));
+                        }
+                        i = (i == hi) ? lo : i + 1;
+                    }
+                    if (step) {
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s)
+                            atomicAdd(&stile[(hs - w0) * NORB + s], __float_as_int(bsum[s] + dith + kMagic) - kMagicBits);
+                    }
+                } else {
+                    for (int i = lo; i <= hi; ++i) {
+                        float wl[4];
+                        tet_weights(T, om[i - w0], wl);
+                        deposit_slow<NORB>(b, wl, A.n_orb, dith, Gc + (i - w0), A.chunk_w, A.status);
+                    }
+                    if (step) {
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s)
+                            if (s < A.n_orb) deposit_one(bsum[s] + dith, Gsc + (long)s * A.chunk_w + (hs - w0), A.status);
+                    }
+                }
+                continue;
             }
             if constexpr (MODE == TETRA_POINT) {
                 TetP TP;
@@ -941,6 +1017,14 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                                   static_cast<unsigned long long>(static_cast<long long>(v)));
                         tile[(j0 + j) * TS + s] = (int)((unsigned)tile[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
                     }
+                    if (MODE == TETRA_INTEGRATED) {
+                        int *se = &stile[(j0 + j) * NORB + s];
+                        if (*se) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(Gsc + (long)s * A.chunk_w + j0 + j),
+                                      static_cast<unsigned long long>(static_cast<long long>(*se)));
+                            *se = 0;
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -974,6 +1058,51 @@ __global__ void tetra_dos_reduce_kernel(const long long *G, int grid_x, int n_or
         long long acc = 0;
         for (int c = 0; c < grid_x; ++c) acc += g[(long)c * n_orb * chunk_w];
         dos[idx] = (float)((double)acc * u);
+    }
+}
+
+// Integrated mode (one energy chunk): block s = orbital s;
+// dos[s][i] = u * (sum over CTAs of the window partials at i + the running sum
+// over i' <= i of the step partials), exact int64 arithmetic up to the scaling.
+__global__ void tetra_dos_reduce_integrated(const long long *G, const long long *Gs, int grid_x, int n_orb,
+                                            int n_omega, int chunk_w, const float *omega, double vtvg,
+                                            int bits, float *dos) {
+    __shared__ long long s_warp[32];
+    __shared__ long long s_carry;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = (int)(blockDim.x >> 5);
+    const double u = fixed_unit(omega, n_omega, TETRA_INTEGRATED, vtvg, bits);
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n_omega; base += blockDim.x) {
+        const int i = base + tid;
+        long long wsum = 0, ssum = 0;
+        if (i < n_omega) {
+            for (int c = 0; c < grid_x; ++c) {
+                const long off = ((long)c * n_orb + s) * chunk_w + i;
+                wsum += G[off];
+                ssum += Gs[off];
+            }
+        }
+        long long x = ssum;   // inclusive scan over the block
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        long long off = s_carry;
+        for (int w2 = 0; w2 < warp; ++w2) off += s_warp[w2];
+        x += off;
+        if (i < n_omega) dos[(long)s * n_omega + i] = (float)((double)(wsum + x) * u);
+        __syncthreads();
+        if (tid == 0) {
+            long long tot = 0;
+            for (int w2 = 0; w2 < nw; ++w2) tot += s_warp[w2];
+            s_carry += tot;
+        }
+        __syncthreads();
     }
 }
 
@@ -1086,8 +1215,9 @@ int norb_template(int n_orb) {
 }
 
 size_t dos_forward_workspace(const Plan &P) {
-    return kStatusBytes +
-           sizeof(long long) * (size_t)P.n_chunks * P.grid_x * P.d.n_orb * (size_t)P.chunk_w;
+    // integrated mode: a second array of the same size for the step sums
+    const size_t parts = sizeof(long long) * (size_t)P.n_chunks * P.grid_x * P.d.n_orb * (size_t)P.chunk_w;
+    return kStatusBytes + (P.d.mode == TETRA_INTEGRATED ? 2 : 1) * parts;
 }
 
 tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w,
@@ -1106,13 +1236,23 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
     A.status = reinterpret_cast<int *>(ws);
     A.queue = nullptr;
     A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
+    A.Gs = A.G + (size_t)P.n_chunks * P.grid_x * P.d.n_orb * (size_t)P.chunk_w;
     cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);
     if (e != cudaSuccess) return TETRA_ECUDA;
     const dim3 grid(P.grid_x, P.n_chunks);
-    e = (P.d.mode == TETRA_POINT)
-            ? launch_norb<TETRA_POINT, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt, A, stream)
-            : launch_norb<TETRA_BIN, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt, A, stream);
+    const int mode = P.d.mode;
+    e = mode == TETRA_POINT ? launch_norb<TETRA_POINT, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt, A, stream)
+        : mode == TETRA_BIN ? launch_norb<TETRA_BIN, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt, A, stream)
+                            : launch_norb<TETRA_INTEGRATED, 1>(P.d.n_orb, P.d.weight_dtype, P.smem_bytes, grid, Bt,
+                                                               A, stream);
     if (e != cudaSuccess) return TETRA_ECUDA;
+    if (mode == TETRA_INTEGRATED) {
+        tetra_dos_reduce_integrated<<<P.d.n_orb, 256, 0, stream>>>(A.G, A.Gs, P.grid_x, P.d.n_orb, P.d.n_omega,
+                                                                   P.chunk_w, omega, Bt.m[0].vtvg,
+                                                                   P.fixed_bits, dos);
+        if (cudaGetLastError() != cudaSuccess) return TETRA_ECUDA;
+        return TETRA_OK;
+    }
     const long total = (long)P.d.n_orb * P.d.n_omega;
     const int rb = 256;
     const int rg = (int)std::min<long>((total + rb - 1) / rb, 4L * P.sm_count);
@@ -1153,6 +1293,7 @@ tetra_status_t launch_dos_batched(const BatchPlan &BP, const float *const *eps, 
     A.status = reinterpret_cast<int *>(ws);
     A.queue = reinterpret_cast<int *>(static_cast<unsigned char *>(ws) + kQueueOffset);
     A.G = reinterpret_cast<long long *>(static_cast<unsigned char *>(ws) + kStatusBytes);
+    A.Gs = nullptr;
     cudaError_t e = cudaMemsetAsync(ws, 0, need, stream);   // status, counter, accumulators
     if (e != cudaSuccess) return TETRA_ECUDA;
     const dim3 grid(BP.grid_x, 1);

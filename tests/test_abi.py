@@ -47,7 +47,7 @@ def test_plan_rejects_bad_descriptions(built):
         T.TetraDesc(4, 4, 4, 0, 1, 10, 0, 0, 0, 0),
         T.TetraDesc(4, 4, 4, 1, 17, 10, 0, 0, 0, 0),
         T.TetraDesc(4, 4, 4, 1, 1, 0, 0, 0, 0, 0),
-        T.TetraDesc(4, 4, 4, 1, 1, 10, 2, 0, 0, 0),
+        T.TetraDesc(4, 4, 4, 1, 1, 10, 3, 0, 0, 0),
         T.TetraDesc(4, 4, 4, 1, 1, 10, 0, 3, 0, 0),
         T.TetraDesc(4, 4, 4, 1, 1, 10, 0, 0, 3, 2),
         T.TetraDesc(4, 4, 4, 1, 1, 10, 0, 0, 0, 9),
