@@ -384,6 +384,39 @@ def paper_shape_workload(torch, T, steps, warmup, local):
                              "(FeSe model, 5 Fe-d orbitals plus the total DOS)"}
 
 
+def integrated_workload(torch, T, n, eps, w, steps, warmup, local):
+    """The orbital occupation n_s(E) (TETRA_INTEGRATED mode) at 1000 energies
+    over the band window, and the Fermi level of half filling (4 of 8 bands),
+    on the benchmark's own eigen-data."""
+    dev = torch.device("cuda", local)
+    nw = 1000
+    plan = T.Plan(n, n, n, 8, 8, nw, mode="integrated", device=local)
+    lo, hi = float(eps[..., :8].min()) - 0.1, float(eps[..., :8].max()) + 0.1
+    import tbgen
+    omega = torch.from_numpy(tbgen.uniform_grid(lo, hi, nw)).to(dev)
+    out = torch.empty((8, nw), dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        plan.dos(eps, w, omega, out=out)
+    torch.cuda.synchronize()
+    s_ = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s_)
+    for _ in range(steps):
+        plan.dos(eps, w, omega, out=out)
+    b.record(s_)
+    torch.cuda.synchronize()
+    assert plan.status() == T.TETRA_OK
+    ms = a.elapsed_time(b) / steps
+    t0 = time.perf_counter()
+    ef = plan.fermi_level(eps, w, 4.0)
+    fermi_s = time.perf_counter() - t0
+    return {"workload": f"occupation n_s(E) at {nw} energies and the Fermi level of 4 electrons per spin, "
+                        f"{n}^3 grid, 8 bands, 8 orbitals, FP32",
+            "integrated_ms": ms, "fermi_level_eV": ef, "fermi_level_seconds": fermi_s,
+            "total_occupation_top": float(out[:, -1].sum())}
+
+
 def cpu_baseline(n, n_omega, seed=0, planes=1, threads=None):
     """The FP64 oracle on the host cores over a bounded sample of the same
     workload: `planes` cube planes (n x n x planes cubes) of the n^3 grid, all
@@ -567,6 +600,8 @@ def main():
         torch.cuda.empty_cache()
         variants["differentiation"] = differentiation_workload(torch, T, args.steps, args.warmup, local)
         variants["paper_shape"] = paper_shape_workload(torch, T, args.steps, args.warmup, local)
+        if args.mode == "point" and args.weight_dtype == "f32":
+            variants["integrated"] = integrated_workload(torch, T, n, eps, w, args.steps, args.warmup, local)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(n, nw, seed=0, planes=1)
