@@ -279,3 +279,34 @@ def fermi_level(eps, n1, n2, n3, n_electrons, tol=1e-12, nthreads: int = 1):
         else:
             hi = mid
     return 0.5 * (lo + hi)
+
+
+# ---------------------------------------------------------------- pair bands (spectral Lindhard function)
+def fermi_dirac(eps, kT, mu):
+    """Occupation 1 / (1 + exp((eps - mu) / kT)) in FP64 (kT > 0)."""
+    x = (np.asarray(eps, np.float64) - mu) / kT
+    return 0.5 * (1.0 - np.tanh(0.5 * x))
+
+
+def pair_bands(eps, n1, n2, n3, q, kT, mu):
+    """Transition "bands" of the bare susceptibility at momentum q (integer
+    grid vector): for every k and band pair (n, m), with j = n * nb + m,
+      energy  Delta_j(k) = eps_m(k + q) - eps_n(k),
+      weight  f(eps_n(k)) - f(eps_m(k + q))     (f: Fermi-Dirac at kT, mu).
+    Their tetrahedron DOS S(q, w) = sum_{n,m} int [f_n - f_m'] delta(w - Delta)
+    is the spectral part of the bare Lindhard function, Im chi0(q, w) = -pi S
+    (the paper names susceptibilities as the method's extension; the energy
+    difference and the occupation difference are linear inside each
+    tetrahedron by the method's own interpolation). Returns (Delta (nk, nb^2),
+    weight (nk, nb^2, 1))."""
+    eps = _c64(eps)
+    nk, nb = eps.shape
+    z, y, x = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    kq = ((x + q[0]) % n1) + n1 * (((y + q[1]) % n2) + n2 * ((z + q[2]) % n3))
+    e_k = eps
+    e_kq = eps[kq.ravel()]
+    f_k = fermi_dirac(e_k, kT, mu)
+    f_kq = fermi_dirac(e_kq, kT, mu)
+    delta = (e_kq[:, None, :] - e_k[:, :, None]).reshape(nk, nb * nb)
+    weight = (f_k[:, :, None] - f_kq[:, None, :]).reshape(nk, nb * nb, 1)
+    return delta, weight

@@ -510,3 +510,36 @@ def test_fermi_level_is_the_root_of_the_count():
                        mode="integrated")[0]
         assert N[0] <= ne + 1e-9 and N[2] >= ne - 1e-9
         assert abs(N[1] - ne) < 1e-6
+
+
+# ---------------------------------------------------------------- spectral Lindhard function
+def test_pair_bands_spectral_function_is_odd_at_q0():
+    """At q = 0 the pairs (n, m) and (m, n) have opposite energies and
+    opposite weights, so S(-w) = -S(w) point by point."""
+    n1, n2, n3, eps, _ = small_problem(seed=4, n=(4, 3, 3), nb=3, norb=1)
+    d, w = oracle.pair_bands(eps, n1, n2, n3, (0, 0, 0), kT=0.2, mu=0.1)
+    E = np.linspace(-3, 3, 61)
+    s = oracle.dos(d, w, n1, n2, n3, E)[0]
+    np.testing.assert_allclose(s, -s[::-1], atol=1e-12 * np.abs(s).max())
+
+
+@pytest.mark.parametrize("q", [(0, 0, 0), (1, 0, 0), (2, 1, 1)])
+def test_pair_bands_spectral_weight_integrates_to_zero(q):
+    """The integral of S over all energies is the grid average of
+    sum_{n,m} [f_n(k) - f_m(k+q)] = nb (<f>_k - <f>_{k+q}) = 0 on a periodic
+    grid (bin mode integrates exactly); the positive part is checked against a
+    direct sum of the occupation differences."""
+    n1, n2, n3, eps, _ = small_problem(seed=6, n=(4, 4, 3), nb=2, norb=1)
+    d, w = oracle.pair_bands(eps, n1, n2, n3, q, kT=0.3, mu=0.0)
+    edges = np.linspace(d.min() - 0.1, d.max() + 0.1, 41)
+    s = oracle.dos(d, w, n1, n2, n3, edges, mode="bin")[0]
+    total = (s * np.diff(edges)).sum()
+    assert abs(total) < 1e-12
+    # the definition, term by term, for one k-point and pair
+    f = oracle.fermi_dirac
+    k = 5
+    z, rem = divmod(k, n1 * n2)
+    y, x = divmod(rem, n1)
+    kq = ((x + q[0]) % n1) + n1 * (((y + q[1]) % n2) + n2 * ((z + q[2]) % n3))
+    assert d[k, 0 * 2 + 1] == eps[kq, 1] - eps[k, 0]
+    assert abs(w[k, 0 * 2 + 1, 0] - (f(eps[k, 0], 0.3, 0.0) - f(eps[kq, 1], 0.3, 0.0))) < 1e-15
