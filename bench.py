@@ -417,6 +417,47 @@ def integrated_workload(torch, T, n, eps, w, steps, warmup, local):
             "total_occupation_top": float(out[:, -1].sum())}
 
 
+def lindhard_workload(torch, T, steps, warmup, local):
+    """Spectral function of the bare susceptibility S(q, w) (tetra_pair_bands +
+    tetra_dos on the 64 transition bands) on the 8-orbital model, 64^3 grid,
+    q = (16, 0, 0), kT = 0.025 eV, chemical potential at 4 electrons per spin,
+    400 energies on [0, 4] eV."""
+    import tbgen
+    dev = torch.device("cuda", local)
+    n = 64
+    p_np, R_np = model_arrays(tbgen.tb_model(0, n_orb=8))
+    plan = T.Plan(n, n, n, 8, 8, 16, device=local)
+    eps, w = plan.eig(torch.from_numpy(p_np).to(dev), torch.from_numpy(R_np).to(dev))
+    mu = plan.fermi_level(eps, w, 4.0)
+    pplan = T.Plan(n, n, n, 64, 1, 400, device=local)
+    ep, wp = pplan.empty_inputs()
+    omega = torch.from_numpy(tbgen.uniform_grid(0.0, 4.0, 400)).to(dev)
+    out = torch.empty((1, 400), dtype=torch.float32, device=dev)
+    from paper_1710_10789_gb300 import tetra_pair_bands, _ptr, _stream_handle
+
+    def step():
+        st = tetra_pair_bands(plan.handle, _ptr(eps), (16, 0, 0), 0.025, mu, pplan.handle, _ptr(ep), _ptr(wp),
+                              _stream_handle(None))
+        assert st == T.TETRA_OK
+        pplan.dos(ep, wp, omega, out=out)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    s_ = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s_)
+    for _ in range(steps):
+        step()
+    b.record(s_)
+    torch.cuda.synchronize()
+    assert pplan.status() == T.TETRA_OK
+    return {"workload": "bare-susceptibility spectral function S(q, w), 8-orbital model, 64^3 grid, "
+                        "q = (16, 0, 0), kT = 0.025 eV, 64 transition bands, 400 energies on [0, 4] eV",
+            "ms_per_evaluation": a.elapsed_time(b) / steps, "chemical_potential_eV": mu}
+
+
 def cpu_baseline(n, n_omega, seed=0, planes=1, threads=None):
     """The FP64 oracle on the host cores over a bounded sample of the same
     workload: `planes` cube planes (n x n x planes cubes) of the n^3 grid, all
@@ -602,6 +643,7 @@ def main():
         variants["paper_shape"] = paper_shape_workload(torch, T, args.steps, args.warmup, local)
         if args.mode == "point" and args.weight_dtype == "f32":
             variants["integrated"] = integrated_workload(torch, T, n, eps, w, args.steps, args.warmup, local)
+        variants["lindhard"] = lindhard_workload(torch, T, args.steps, args.warmup, local)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(n, nw, seed=0, planes=1)

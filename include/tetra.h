@@ -274,6 +274,27 @@ size_t tetra_fermi_workspace_bytes(tetra_plan_t plan);
 tetra_status_t tetra_fermi_level(tetra_plan_t plan, const float *eps, const void *w, double n_electrons,
                                  float *ef, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Transition bands of the bare susceptibility at momentum q (the extension
+ * to susceptibilities the paper names as future work; not in the paper).
+ * For every point k of the plan's grid and band pair (n, m), stored as band
+ * j = n * n_bands + m of pair_plan:
+ *   eps_pairs : eps_m(k + q) - eps_n(k),
+ *   w_pairs   : f(eps_n(k)) - f(eps_m(k + q)),  f(e) = 1 / (1 + e^{(e - mu)/kT}).
+ * tetra_dos on pair_plan (point mode, energies w) then gives the spectral
+ * function S(q, w) = sum_{n,m} int [f_n(k) - f_m(k+q)] delta(w - eps_m(k+q)
+ * + eps_n(k)) dk / V_G of the bare Lindhard function, Im chi0(q, w + i0) =
+ * -pi S(q, w): both differences are linear inside a tetrahedron by the
+ * method's own interpolation. Only the spectral (imaginary) part is provided.
+ *   plan      : the bands (n_bands <= 8), eps in its tetra layout.
+ *   q         : integer grid vector (q_i in units of 2 pi / n_i), any sign.
+ *   kT, mu    : temperature (> 0) and chemical potential, in energy units.
+ *   pair_plan : same grid, n_bands = plan n_bands^2, n_orb = 1, TETRA_F32;
+ *               eps_pairs / w_pairs in its tetra layout (halo points written).
+ * Returns TETRA_EINVAL for mismatched plans, kT <= 0, null or misaligned
+ * pointers, TETRA_EUNSUPPORTED for slab plans or n_bands > 8. */
+tetra_status_t tetra_pair_bands(tetra_plan_t plan, const float *eps, const int q[3], float kT, float mu,
+                                tetra_plan_t pair_plan, float *eps_pairs, float *w_pairs, cudaStream_t stream);
+
 /* Device-side status recorded in a workspace by the last call that used it
  * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. */
 tetra_status_t tetra_workspace_status(const void *ws, cudaStream_t stream);

@@ -26,7 +26,7 @@ __all__ = [
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc", "Plan",
     "EXPORTED_SYMBOLS", "TetraTune", "tetra_plan_batched", "tetra_batch_plan_destroy",
     "tetra_batch_layout", "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
-    "BatchPlan", "TETRA_MAX_BATCH", "tetra_fermi_workspace_bytes", "tetra_fermi_level",
+    "BatchPlan", "TETRA_MAX_BATCH", "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
 ]
 
 TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = (
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc",
     "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
     "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
-    "tetra_fermi_workspace_bytes", "tetra_fermi_level",
+    "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
 )
 TETRA_MAX_BATCH = 64
 
@@ -126,6 +126,8 @@ def lib():
             L.tetra_fermi_workspace_bytes.restype = sz
             L.tetra_fermi_level.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
                                             vp, sz, vp]
+            L.tetra_pair_bands.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_float,
+                                           ctypes.c_float, vp, vp, vp, vp]
             L.tetra_strerror.argtypes = [i]
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
@@ -134,7 +136,7 @@ def lib():
                          "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
                          "tetra_workspace_status", "tetra_plan_batched",
                          "tetra_batch_plan_destroy", "tetra_batch_layout", "tetra_batch_info",
-                         "tetra_dos_batched", "tetra_fermi_level"):
+                         "tetra_dos_batched", "tetra_fermi_level", "tetra_pair_bands"):
                 getattr(L, name).restype = i
             _LIB = L
     return _LIB
@@ -176,6 +178,11 @@ def tetra_fermi_workspace_bytes(plan) -> int:
 
 def tetra_fermi_level(plan, eps, w, n_electrons, ef, ws, ws_bytes, stream) -> int:
     return lib().tetra_fermi_level(plan, eps, w, float(n_electrons), ef, ws, ws_bytes, stream)
+
+
+def tetra_pair_bands(plan, eps, q, kT, mu, pair_plan, eps_pairs, w_pairs, stream) -> int:
+    qa = (ctypes.c_int * 3)(*[int(v) for v in q])
+    return lib().tetra_pair_bands(plan, eps, qa, float(kT), float(mu), pair_plan, eps_pairs, w_pairs, stream)
 
 
 def tetra_dos_noalloc(plan, eps, w, omega, dos, stream) -> int:
@@ -351,6 +358,14 @@ class Plan:
         _check(tetra_fermi_level(self.handle, _ptr(eps), _ptr(w), n_electrons, ctypes.byref(ef), _ptr(ws),
                                  ws.numel(), _stream_handle(stream)), "tetra_fermi_level")
         return float(ef.value)
+
+    def pair_bands(self, eps, q, kT, mu, pair_plan, stream=None):
+        """Transition bands of the bare susceptibility at grid vector q
+        (tetra_pair_bands) in pair_plan's layout: (eps_pairs, w_pairs)."""
+        eps_p, w_p = pair_plan.empty_inputs()
+        _check(tetra_pair_bands(self.handle, _ptr(eps), q, kT, mu, pair_plan.handle, _ptr(eps_p), _ptr(w_p),
+                                _stream_handle(stream)), "tetra_pair_bands")
+        return eps_p, w_p
 
     def _model(self, params, R):
         n_orb = self.desc.n_bands

@@ -182,6 +182,8 @@ tetra_status_t launch_dos_backward(const Plan &P, const float *eps, const void *
 size_t dos_backward_workspace(const Plan &P);
 tetra_status_t launch_eig(const Plan &P, const tetra_model_t *m, float *eps, void *w,
                           cudaStream_t stream);
+tetra_status_t launch_pair_bands(const Plan &P, const float *eps, const int q[3], float kT, float mu,
+                                 const Plan &Q, float *eps_p, float *w_p, cudaStream_t stream);
 tetra_status_t launch_eig_backward(const Plan &P, const tetra_model_t *m, const float *geps,
                                    const float *gw, float *gparams, void *ws, size_t ws_bytes,
                                    cudaStream_t stream);
