@@ -65,13 +65,16 @@ int pow2_floor(int v) {
     return p;
 }
 
-// Default box of cubes for a band count: 4 x 4 x BZ with at most ~1536
-// (tetrahedron, band) items per box, which keeps the per-item fixed-point cap
-// of the int32 tile (2^30 / items) above typical values.
+// Default box of cubes for a band count: 4 x 4 x BZ with at most ~1536 work
+// items per box (a work item is a (tetrahedron pair, band) in point mode with up
+// to 8 orbitals, a (tetrahedron, band) otherwise), which keeps the per-item
+// fixed-point cap of the int32 tile (2^30 / items) above typical values.
 void default_box(const tetra_desc_t &d, int box[3]) {
+    const bool pairs = d.mode == TETRA_POINT && tetra::norb_template(d.n_orb) <= 8;
+    const int per_cube = (pairs ? 3 : 6) * std::max(1, d.n_bands);
     box[0] = env_int("TETRA_BOX_X", 4);
     box[1] = env_int("TETRA_BOX_Y", 4);
-    box[2] = env_int("TETRA_BOX_Z", std::max(1, std::min(4, 1536 / (96 * std::max(1, d.n_bands)))));
+    box[2] = env_int("TETRA_BOX_Z", std::max(1, std::min(4, 1536 / (16 * per_cube))));
 }
 
 // Chooses the box shape, energy chunking and grid of the forward kernel. Box
@@ -87,19 +90,20 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     P.nbz = (P.z1 - P.z0 + P.BZ - 1) / P.BZ;
     P.n_boxes = P.nbx * P.nby * P.nbz;
     const size_t npts = (size_t)(P.BX + 1) * (P.BY + 1) * (P.BZ + 1);
-    const size_t e_off = (npts * P.eps_stride * 4 + 127) & ~size_t(127);
-    const size_t stage = (e_off + npts * P.w_stride * P.wbytes + 127) & ~size_t(127);
+    // TMA slots (128-byte multiples): two of a box's energies, one of its weights
+    const size_t e_stage = (npts * P.eps_stride * 4 + 127) & ~size_t(127);
+    const size_t w_stage = (npts * P.w_stride * P.wbytes + 127) & ~size_t(127);
     // point mode with up to 8 orbitals: one item per face-sharing tetrahedron
     // pair (3 per cube); otherwise one item per tetrahedron (6 per cube)
     const bool pairs = d.mode == TETRA_POINT && tetra::norb_template(d.n_orb) <= 8;
     P.items_per_box = (pairs ? 3 : 6) * P.BX * P.BY * P.BZ * d.n_bands;
     if (P.items_per_box > 65535) return TETRA_EUNSUPPORTED;
     P.tile_stride = tetra::norb_template(d.n_orb) + 1;
-    // two TMA stages, per-item sort arrays, length histogram and cursors,
+    // TMA slots, per-item sort arrays, length histogram and cursors, three
     // mbarriers, alignment slack, the kernel's static variables and the tile's
     // extra row
-    const size_t fixed = 2 * stage + 6 * (size_t)P.items_per_box + 16 + 2 * 256 * 4 + 32 + 1024 + 512 + 128 +
-                         4 * (size_t)P.tile_stride;
+    const size_t fixed = 2 * e_stage + w_stage + 6 * (size_t)P.items_per_box + 16 + 2 * 256 * 4 + 40 + 1024 +
+                         512 + 128 + 4 * (size_t)P.tile_stride;
     // per energy: int tile row, cached energy, 1/width (bin mode), block bound share
     // (integrated mode: plus a row of per-orbital step sums)
     const size_t per_w = 4 * (size_t)(P.tile_stride + 1 + (d.mode == TETRA_BIN ? 1 : 0) +

@@ -109,7 +109,8 @@ struct FwdArgs {
     int BX, BY, BZ;
     int lbx, lby, lbz;   // log2 of the box sides (powers of two)
     int eps_stride, w_stride;
-    uint32_t e_box_bytes, w_box_bytes, w_box_off, stage_bytes;   // w box at stage + w_box_off (128-aligned)
+    uint32_t e_box_bytes, w_box_bytes;   // TMA bytes of a box's energies / weights
+    uint32_t e_stage, w_stage;           // their shared-memory slots (128-byte multiples)
     int chunk_w;         // energies per shared tile (largest model of a batch)
     int items_per_box;   // items per box: (pair, band) in point mode, (tetrahedron, band) otherwise
     int fast_cap;
@@ -415,8 +416,12 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     const int tid = threadIdx.x;
     const int chunk = blockIdx.y;   // energy chunk (single-model launches)
     // shared memory carve-up
-    unsigned char *stage[2] = {smem, smem + A.stage_bytes};
-    int *tile = reinterpret_cast<int *>(smem + 2 * A.stage_bytes);   // [chunk_w + 1][TS]
+    // energies of two boxes (pass A of box k+1 needs no weights) and the
+    // weights of one box, refilled after pass B and loaded while the next
+    // box's pass A and ranking run
+    unsigned char *estage[2] = {smem, smem + A.e_stage};
+    unsigned char *wstage = smem + 2 * A.e_stage;
+    int *tile = reinterpret_cast<int *>(wstage + A.w_stage);   // [chunk_w + 1][TS]
     // integrated mode: per-orbital sums of the saturated weights of the items
     // whose E4 lies between energy j-1 and j, [chunk_w][NORB] (plain integers)
     int *stile = tile + TS * (A.chunk_w + 1);
@@ -436,14 +441,14 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     __shared__ int s_wsum[kMaxThreads / 32];
     __shared__ int s_abort, s_active, s_slot;
     __shared__ int s_cdelta[8];   // staged-box point offset of cube corner c
+    __shared__ int n_issued[3];   // TMA loads issued per mbarrier (thread 0 keeps them)
 
     // self-check of the shared-memory carve-up against the launch's dynamic size
     {
-        const uintptr_t need = reinterpret_cast<uintptr_t>(mbar + 2) - reinterpret_cast<uintptr_t>(smem_raw);
-        const bool bad = need > dynamic_smem_bytes() || (smem_u32(stage[0]) & 127u) != 0 ||
-                         (smem_u32(stage[1]) & 127u) != 0 || (A.w_box_off & 127u) != 0 ||
-                         A.w_box_off < A.e_box_bytes || A.w_box_off + A.w_box_bytes > A.stage_bytes ||
-                         (smem_u32(mbar) & 7u) != 0 || A.items_per_box > 65535;
+        const uintptr_t need = reinterpret_cast<uintptr_t>(mbar + 3) - reinterpret_cast<uintptr_t>(smem_raw);
+        const bool bad = need > dynamic_smem_bytes() || (smem_u32(estage[0]) & 127u) != 0 ||
+                         (A.e_stage & 127u) != 0 || (A.w_stage & 127u) != 0 || A.e_box_bytes > A.e_stage ||
+                         A.w_box_bytes > A.w_stage || (smem_u32(mbar) & 7u) != 0 || A.items_per_box > 65535;
         if (bad) {
             if (tid == 0) atomicOr(A.status, kFlagConfig);
             return;
@@ -453,8 +458,10 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         s_cdelta[tid] = (tid & 1) + (A.BX + 1) * (((tid >> 1) & 1) + (A.BY + 1) * (tid >> 2));
     if (tid == 0) {
         s_abort = 0;
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        mbar_init(&mbar[0], 1);   // energies, stage 0
+        mbar_init(&mbar[1], 1);   // energies, stage 1
+        mbar_init(&mbar[2], 1);   // weights
+        n_issued[0] = n_issued[1] = n_issued[2] = 0;
         fence_mbar_init();
     }
 
@@ -478,7 +485,8 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         box = g - B.m[m].box_base;
         return true;
     };
-    auto issue = [&](int k, int stg) {   // thread 0 only
+    // energies of work item k into energy stage stg (claims the item in a batch)
+    auto issue_e = [&](int k, int stg) {   // thread 0 only
         if (MAXM > 1) {
             const int g = atomicAdd(A.queue, 1);
             s_work[k & 3] = g < B.total_work ? g : -1;
@@ -487,16 +495,26 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         if (!work(k, mi, box)) return;
         const ModelP &Mk = B.m[mi];
         const int ix = box % Mk.nbx, iy = (box / Mk.nbx) % Mk.nby, iz = box / (Mk.nbx * Mk.nby);
-        mbar_arrive_expect_tx(&mbar[stg], A.e_box_bytes + A.w_box_bytes);
-        tma_load_4d(stage[stg], &B.maps[mi].e, 0, ix * A.BX, iy * A.BY, Mk.z0 + iz * A.BZ, &mbar[stg]);
-        tma_load_4d(stage[stg] + A.w_box_off, &B.maps[mi].w, 0, ix * A.BX, iy * A.BY,
-                    Mk.z0 + iz * A.BZ, &mbar[stg]);
+        ++n_issued[stg];
+        mbar_arrive_expect_tx(&mbar[stg], A.e_box_bytes);
+        tma_load_4d(estage[stg], &B.maps[mi].e, 0, ix * A.BX, iy * A.BY, Mk.z0 + iz * A.BZ, &mbar[stg]);
+    };
+    // weights of work item k (already claimed) into the weight stage
+    auto issue_w = [&](int k) {   // thread 0 only
+        int mi, box;
+        if (!work(k, mi, box)) return;
+        const ModelP &Mk = B.m[mi];
+        const int ix = box % Mk.nbx, iy = (box / Mk.nbx) % Mk.nby, iz = box / (Mk.nbx * Mk.nby);
+        ++n_issued[2];
+        mbar_arrive_expect_tx(&mbar[2], A.w_box_bytes);
+        tma_load_4d(wstage, &B.maps[mi].w, 0, ix * A.BX, iy * A.BY, Mk.z0 + iz * A.BZ, &mbar[2]);
     };
     __syncthreads();
-    // prologue: first two work items
+    // prologue: energies of the first two work items, weights of the first
     if (tid == 0) {
-        issue(0, 0);
-        issue(1, 1);
+        issue_e(0, 0);
+        issue_e(1, 1);
+        issue_w(0);
     }
     __syncthreads();
 
@@ -636,35 +654,12 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             s_abort = 1;
             break;
         }
-        const float *Es = reinterpret_cast<const float *>(stage[st]);
-        const WT *Ws = reinterpret_cast<const WT *>(stage[st] + A.w_box_off);
+        const float *Es = reinterpret_cast<const float *>(estage[st]);
+        const WT *Ws = reinterpret_cast<const WT *>(wstage);
         const int ix = box % M.nbx, iy = (box / M.nbx) % M.nby, iz = box / (M.nbx * M.nby);
         const int gx0 = ix * A.BX, gy0 = iy * A.BY, gz0 = M.z0 + iz * A.BZ;
         const int lane = tid & 31, warp = tid >> 5, nwarp = (int)(blockDim.x >> 5);
 
-        // Bmax = max |w| over the staged box (all of it, padding included, so it
-        // bounds every orbital weight an item can read)
-        float bmax = 0.f;
-        {
-            const int n16 = (int)(A.w_box_bytes >> 4);
-            const uint4 *src = reinterpret_cast<const uint4 *>(stage[st] + A.w_box_off);
-            for (int i = tid; i < n16; i += blockDim.x) {
-                const uint4 v = src[i];
-                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (sizeof(WT) == 4) {
-                        bmax = fmaxf(bmax, fabsf(__uint_as_float(wv[q])));
-                    } else {
-                        const WT lo = *reinterpret_cast<const WT *>(&wv[q]);
-                        const WT hi = *(reinterpret_cast<const WT *>(&wv[q]) + 1);
-                        bmax = fmaxf(bmax, fmaxf(fabsf(to_f32<WT>(lo)), fabsf(to_f32<WT>(hi))));
-                    }
-                }
-            }
-        }
-        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-        if (lane == 0) red_f[warp] = bmax;
 
         // Pass A: window of every item (corner min / max only) and a histogram
         // of its length K, so that pass B can hand items of similar length to
@@ -727,8 +722,6 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             for (int j = 0; j < PER; ++j) { kcursor[tid * PER + j] = run; run += v[j]; }
             if (tid == 31) s_active = x;
         }
-        bmax = 0.f;
-        for (int i = 0; i < nwarp; ++i) bmax = fmaxf(bmax, red_f[i]);
         __syncthreads();
         for (int base = warp * 32; base < A.items_per_box; base += nwarp * 32) {
             const int it = base + lane;
@@ -737,7 +730,37 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                              (K > 0 || (MODE == TETRA_INTEGRATED && s_lo[it] + K < wc));
             if (act) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
         }
-        __syncthreads();
+        // the box's weights (loaded while pass A and the ranking ran), and
+        // Bmax = max |w| over them (all of the box, padding included, so it
+        // bounds every orbital weight an item can read)
+        const bool okw = mbar_wait_bounded(&mbar[2], k & 1, A.status);
+        float bmax = 0.f;
+        if (okw) {
+            const int n16 = (int)(A.w_box_bytes >> 4);
+            const uint4 *src = reinterpret_cast<const uint4 *>(wstage);
+            for (int i = tid; i < n16; i += blockDim.x) {
+                const uint4 v = src[i];
+                const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (sizeof(WT) == 4) {
+                        bmax = fmaxf(bmax, fabsf(__uint_as_float(wv[q])));
+                    } else {
+                        const WT lo = *reinterpret_cast<const WT *>(&wv[q]);
+                        const WT hi = *(reinterpret_cast<const WT *>(&wv[q]) + 1);
+                        bmax = fmaxf(bmax, fmaxf(fabsf(to_f32<WT>(lo)), fabsf(to_f32<WT>(hi))));
+                    }
+                }
+            }
+        }
+        for (int o = 16; o; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        if (lane == 0) red_f[warp] = bmax;
+        if (__syncthreads_or(!okw)) {
+            s_abort = 1;
+            break;
+        }
+        bmax = 0.f;
+        for (int i = 0; i < nwarp; ++i) bmax = fmaxf(bmax, red_f[i]);
         const int n_active = s_active;
         const int n_slots = (n_active + 31) >> 5;
 
@@ -992,11 +1015,12 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 }
             }
         }
-        __syncthreads();   // every thread is done reading stage[st] and adding to the tile
-        // refill this stage with work item k+2
+        __syncthreads();   // every thread is done reading both stages and adding to the tile
+        // refill: energies of work item k+2 into this energy stage, weights of k+1
         if (tid == 0) {
             fence_proxy_async_smem();
-            issue(k + 2, st);
+            issue_e(k + 2, st);
+            issue_w(k + 1);
         }
         // A block whose bound reached flush_at is moved into the CTA's int64
         // partial before the next box: one box adds less than 2^30 - 2^20 to any
@@ -1037,7 +1061,9 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     if (s_abort) {
         // a TMA wait timed out: wait (bounded) for copies still in flight, then leave
         if (tid == 0) {
-            for (int k = 0; k < 2; ++k) mbar_wait_bounded(&mbar[k], 0, nullptr, 100000000ull);
+            for (int b = 0; b < 3; ++b)
+                if (n_issued[b] > 0)
+                    mbar_wait_bounded(&mbar[b], (uint32_t)(n_issued[b] - 1) & 1u, nullptr, 100000000ull);
         }
         return;
     }
@@ -1176,8 +1202,8 @@ void fill_common(const Plan &P, FwdArgs &A) {
     A.e_box_bytes = npts * P.eps_stride * 4u;
     A.w_box_bytes = npts * P.w_stride * (uint32_t)P.wbytes;
     // every TMA destination starts on a 128-byte boundary
-    A.w_box_off = (A.e_box_bytes + 127u) & ~127u;
-    A.stage_bytes = (A.w_box_off + A.w_box_bytes + 127u) & ~127u;
+    A.e_stage = (A.e_box_bytes + 127u) & ~127u;
+    A.w_stage = (A.w_box_bytes + 127u) & ~127u;
     A.chunk_w = P.chunk_w;
     A.items_per_box = P.items_per_box;
     A.flush_at = 1u << P.flush_bits;
