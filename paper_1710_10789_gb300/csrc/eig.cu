@@ -6,10 +6,11 @@
 // One thread owns one k-point: it builds H(k) = diag(onsite) +
 // sum_r [t_r e^{ik.R_r} + h.c.] from the model staged in shared memory,
 // reduces it to real tridiagonal form by Householder reflections and
-// diagonalises that by implicit-shift QR, with H, the accumulated unitary and
-// the tridiagonal in registers (all indices compile-time after unrolling),
-// then sorts the eigenpairs with a transposition network and stores
-// eps_n and |V_sn|^2.
+// diagonalises that by implicit-shift QR, with H, the reflectors, the
+// accumulated rotations and the tridiagonal in registers (all indices
+// compile-time after unrolling), forms each eigenvector by applying the
+// reflectors to a column of the rotations, then sorts the eigenpairs with a
+// transposition network and stores eps_n and |V_sn|^2.
 #include "eig_common.cuh"
 
 namespace tetra {
@@ -20,12 +21,10 @@ using namespace eigdetail;
 
 template <int N, typename WT>
 __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A) {
-    __shared__ float s_par[N + 2 * kMaxR * N * N];
+    __shared__ float s_on[N];
+    __shared__ float4 s_hop[kMaxR * n_upper<N>()];
     __shared__ int s_R[3 * kMaxR];
-    const int npar = N + 2 * A.n_R * N * N;
-    for (int i = threadIdx.x; i < npar; i += blockDim.x) s_par[i] = A.params[i];
-    for (int i = threadIdx.x; i < 3 * A.n_R; i += blockDim.x)
-        s_R[i] = reduce_mod(A.R[i], i % 3 == 0 ? A.n1 : (i % 3 == 1 ? A.n2 : A.n3));
+    stage_model<N>(A.params, A.R, A.n_R, A.n1, A.n2, A.n3, s_on, s_hop, s_R);
     __syncthreads();
     const long P = (long)A.nx * A.ny * A.nz;
     const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -37,7 +36,7 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
     Herm<N> M;
     {
         Mat<N> H;   // upper triangle of H(k)
-        build_h<N>(H, s_par, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
+        build_h<N>(H, s_on, s_hop, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -57,8 +56,10 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
 #pragma unroll
         for (int n = 0; n < N; ++n) {
             ev[n] = M.d[n];
+            float vr[N], vi[N];
+            eigvec_column<N>(M, n, vr, vi);
 #pragma unroll
-            for (int s = 0; s < N; ++s) W[n][s] = M.qr[s][n] * M.qr[s][n] + M.qi[s][n] * M.qi[s][n];
+            for (int s = 0; s < N; ++s) W[n][s] = vr[s] * vr[s] + vi[s] * vi[s];
         }
     }
     // eigenvalues and weights, sorted ascending (odd-even transposition network)

@@ -37,7 +37,8 @@ struct EigBwdArgs {
 template <int N>
 __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) {
     extern __shared__ __align__(16) float sm[];
-    __shared__ float s_par[N + 2 * kMaxR * N * N];
+    __shared__ float s_on[N];
+    __shared__ float4 s_hop[kMaxR * n_upper<N>()];
     __shared__ int s_R[3 * kMaxR];
     constexpr int NN2 = 2 * N * N;   // complex N x N as (re, im) pairs
     float *Vs = sm;                  // [kBT][NN2]  eigenvectors V[s][j]
@@ -46,10 +47,7 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
     float *Ph = Xs + kBT * NN2;      // [kBT][2 n_R] e^{ik.R}
     double *acc = reinterpret_cast<double *>(Ph + kBT * 2 * kMaxR);   // [n_out] block sums
     const int tid = threadIdx.x;
-    const int npar = N + 2 * A.n_R * N * N;
-    for (int i = tid; i < npar; i += blockDim.x) s_par[i] = A.params[i];
-    for (int i = tid; i < 3 * A.n_R; i += blockDim.x)
-        s_R[i] = reduce_mod(A.R[i], i % 3 == 0 ? A.n1 : (i % 3 == 1 ? A.n2 : A.n3));
+    stage_model<N>(A.params, A.R, A.n_R, A.n1, A.n2, A.n3, s_on, s_hop, s_R);
     __syncthreads();
     const long nk = (long)A.n1 * A.n2 * A.n3;
     // outputs owned by this thread: o = tid, tid + kBT, ... (accumulated in acc[o])
@@ -66,7 +64,7 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
             Herm<N> M;
             {
                 Mat<N> H;
-                build_h<N>(H, s_par, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
+                build_h<N>(H, s_on, s_hop, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
 #pragma unroll
                 for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -83,6 +81,7 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
             } else {
                 householder_tridiag<N>(M);
                 tridiag_qr<N>(M);
+                eigenvectors<N>(M);
 #pragma unroll
                 for (int j = 0; j < N; ++j) lam[j] = M.d[j];
 #pragma unroll

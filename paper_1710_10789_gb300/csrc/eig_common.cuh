@@ -45,32 +45,58 @@ __device__ __forceinline__ void phase(const int *R, int x, int y, int z, int n1,
     sincospif(2.0f * frac, &sn, &cs);
 }
 
-// H(k) at grid point (x, y, z) from the model staged in shared memory
-// (s_par: onsite[N], Re t[n_R][N][N], Im t[n_R][N][N]; s_R: R[n_R][3] reduced
-// mod (n1, n2, n3));
-// upper triangle into M.
+// Upper-triangle entries (i <= j) of an N x N matrix, row by row.
 template <int N>
-__device__ __forceinline__ void build_h(Mat<N> &M, const float *s_par, const int *s_R, int n_R,
-                                        int x, int y, int z, int n1, int n2, int n3) {
+__host__ __device__ constexpr int n_upper() { return N * (N + 1) / 2; }
+
+// The model as build_h reads it, staged in shared memory by every thread of
+// the block: s_on[N] on-site energies; s_hop[n_R][n_upper] per hopping r and
+// upper-triangle pair (i, j) the sums and differences of t_ij and t_ji,
+// {Re(t_ij + t_ji), Im(t_ij + t_ji), Re(t_ij - t_ji), Im(t_ij - t_ji)}
+// (params: onsite[N], Re t[n_R][N][N], Im t[n_R][N][N]); s_R[n_R][3] the
+// lattice vectors reduced mod (n1, n2, n3).
+template <int N>
+__device__ __forceinline__ void stage_model(const float *params, const int *R, int n_R, int n1,
+                                            int n2, int n3, float *s_on, float4 *s_hop, int *s_R) {
+    constexpr int NP = n_upper<N>();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s_on[i] = params[i];
+    const float *tre = params + N, *tim = params + N + n_R * N * N;
+    for (int idx = threadIdx.x; idx < n_R * NP; idx += blockDim.x) {
+        const int r = idx / NP;
+        int i = 0, rem = idx - r * NP;
+        while (rem >= N - i) { rem -= N - i; ++i; }
+        const int j = i + rem;
+        const float ar = tre[r * N * N + i * N + j], ai = tim[r * N * N + i * N + j];
+        const float br = tre[r * N * N + j * N + i], bi = tim[r * N * N + j * N + i];
+        s_hop[idx] = make_float4(ar + br, ai + bi, ar - br, ai - bi);
+    }
+    for (int i = threadIdx.x; i < 3 * n_R; i += blockDim.x)
+        s_R[i] = reduce_mod(R[i], i % 3 == 0 ? n1 : (i % 3 == 1 ? n2 : n3));
+}
+
+// H(k) at grid point (x, y, z) from the staged model (stage_model), upper
+// triangle into M. Term r adds t_ij e^{i th} + conj(t_ji) e^{-i th}
+// = (S_re c - S_im s) + i (D_re s + D_im c), th = k.R_r, S = t_ij + t_ji,
+// D = t_ij - t_ji.
+template <int N>
+__device__ __forceinline__ void build_h(Mat<N> &M, const float *s_on, const float4 *s_hop,
+                                        const int *s_R, int n_R, int x, int y, int z, int n1,
+                                        int n2, int n3) {
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int j = i; j < N; ++j) { M.hr[i][j] = (i == j) ? s_par[i] : 0.f; M.hi[i][j] = 0.f; }
-    const float *tre = s_par + N;
-    const float *tim = s_par + N + n_R * N * N;
+        for (int j = i; j < N; ++j) { M.hr[i][j] = (i == j) ? s_on[i] : 0.f; M.hi[i][j] = 0.f; }
     for (int r = 0; r < n_R; ++r) {
         float sn, cs;
         phase(s_R + 3 * r, x, y, z, n1, n2, n3, sn, cs);
-        const float *Tr = tre + r * N * N, *Ti = tim + r * N * N;
+        const float4 *h = s_hop + r * n_upper<N>();
 #pragma unroll
-        for (int i = 0; i < N; ++i)
+        for (int i = 0, q = 0; i < N; ++i)
 #pragma unroll
-            for (int j = i; j < N; ++j) {
-                // t_ij e^{i th} + conj(t_ji) e^{-i th}
-                const float ar = Tr[i * N + j], ai = Ti[i * N + j];
-                const float br = Tr[j * N + i], bi = Ti[j * N + i];
-                M.hr[i][j] += (ar * cs - ai * sn) + (br * cs - bi * sn);
-                M.hi[i][j] += (ar * sn + ai * cs) - (br * sn + bi * cs);
+            for (int j = i; j < N; ++j, ++q) {
+                const float4 t = h[q];
+                M.hr[i][j] = fmaf(t.x, cs, fmaf(-t.y, sn, M.hr[i][j]));
+                M.hi[i][j] = fmaf(t.z, sn, fmaf(t.w, cs, M.hi[i][j]));
             }
     }
 #pragma unroll
@@ -91,23 +117,22 @@ namespace eigdetail {
 template <int N>
 struct Herm {
     float ar[N][N], ai[N][N];   // lower triangle of A used (i >= j)
-    float qr[N][N], qi[N][N];   // unitary Q, A = Q T Q^H; then the eigenvectors (columns)
+    float ur[N][N], ui[N][N];   // reflector k (k <= N-3) in row k, entries k+1 .. N-1
+    float sr[N], si[N];         // unitary diagonal scaling delta
     float g[N][N];              // real orthogonal G of the QR phase, T = G diag(d) G^T
     float d[N], e[N];           // real tridiagonal T: diagonal, sub-diagonal e[0..N-2]
+    float qr[N][N], qi[N][N];   // eigenvectors (columns), when formed by eigenvectors()
 };
 
-// A (lower triangle) -> d, e real and Q with A = Q T Q^H.
-// Step k reflects x = A[k+1..N-1][k] onto alpha e_1 with H = I - 2 u u^H,
-// alpha = -(x_0/|x_0|) |x| (no cancellation in v_0 = x_0 - alpha), applies
+// A (lower triangle) -> d, e real and Q = H_0 H_1 ... H_{N-3} diag(delta) with
+// A = Q T Q^H; the reflectors H_k = I - 2 u_k u_k^H and delta are kept, Q is
+// not formed. Step k reflects x = A[k+1..N-1][k] onto alpha e_1,
+// alpha = -(x_0/|x_0|) |x| (no cancellation in v_0 = x_0 - alpha), and applies
 // A <- H A H to the trailing block as A -= 2 (u w^H + w u^H), w = p - (u^H p) u,
-// p = A u, and Q <- Q H. Columns whose entries below the sub-diagonal are at
-// the FP32 resolution of ||A|| are left as they are (those entries dropped).
+// p = A u. Columns whose entries below the sub-diagonal are at the FP32
+// resolution of ||A|| are left as they are (those entries dropped; u_k = 0).
 template <int N>
 __device__ __forceinline__ void householder_tridiag(Herm<N> &M) {
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-        for (int j = 0; j < N; ++j) { M.qr[i][j] = (i == j) ? 1.f : 0.f; M.qi[i][j] = 0.f; }
     float fro = 0.f;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -138,6 +163,8 @@ __device__ __forceinline__ void householder_tridiag(Herm<N> &M) {
         ui[k + 1] = phi * t0 * iv;
 #pragma unroll
         for (int j = k + 2; j < N; ++j) { ur[j] = M.ar[j][k] * iv; ui[j] = M.ai[j][k] * iv; }
+#pragma unroll
+        for (int j = k + 1; j < N; ++j) { M.ur[k][j] = ur[j]; M.ui[k][j] = ui[j]; }
         // p = A_s u (A_s Hermitian, lower storage)
         float pr[N], pi[N];
 #pragma unroll
@@ -172,22 +199,6 @@ __device__ __forceinline__ void householder_tridiag(Herm<N> &M) {
                 M.ar[i][j] = fmaf(-2.f, cr, M.ar[i][j]);
                 if (i != j) M.ai[i][j] = fmaf(-2.f, ci, M.ai[i][j]);
             }
-        // Q[:, k+1..] <- Q[:, k+1..] (I - 2 u u^H)
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-            float tr = 0.f, ti = 0.f;   // (Q u)_r
-#pragma unroll
-            for (int j = k + 1; j < N; ++j) {
-                tr = fmaf(M.qr[r][j], ur[j], fmaf(-M.qi[r][j], ui[j], tr));
-                ti = fmaf(M.qr[r][j], ui[j], fmaf(M.qi[r][j], ur[j], ti));
-            }
-#pragma unroll
-            for (int j = k + 1; j < N; ++j) {
-                // Q_rj -= 2 t_r conj(u_j)
-                M.qr[r][j] = fmaf(-2.f, tr * ur[j] + ti * ui[j], M.qr[r][j]);
-                M.qi[r][j] = fmaf(-2.f, ti * ur[j] - tr * ui[j], M.qi[r][j]);
-            }
-        }
     }
     if constexpr (N > 1) {
         er[N - 2] = M.ar[N - 1][N - 2];
@@ -196,18 +207,12 @@ __device__ __forceinline__ void householder_tridiag(Herm<N> &M) {
 #pragma unroll
     for (int k = 0; k < N; ++k) M.d[k] = M.ar[k][k];
     // unitary diagonal scaling that makes the sub-diagonal real and >= 0:
-    // delta_{k+1} = delta_k e_k / |e_k|, Q <- Q diag(delta)
+    // delta_0 = 1, delta_{k+1} = delta_k e_k / |e_k|
     float dr = 1.f, di = 0.f;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        if (k > 0) {
-#pragma unroll
-            for (int r = 0; r < N; ++r) {
-                const float a = M.qr[r][k], b = M.qi[r][k];
-                M.qr[r][k] = a * dr - b * di;
-                M.qi[r][k] = a * di + b * dr;
-            }
-        }
+        M.sr[k] = dr;
+        M.si[k] = di;
         if (k + 1 < N) {
             const float ae = sqrtf(er[k] * er[k] + ei[k] * ei[k]);
             const float ie = ae > 0.f ? 1.f / ae : 0.f;
@@ -222,7 +227,7 @@ __device__ __forceinline__ void householder_tridiag(Herm<N> &M) {
 
 // Implicit-shift QR on the real tridiagonal (d, e), the real rotations
 // accumulated into G (started at the identity; the eigenvectors of H are the
-// columns of Q G, formed once at the end). Deflation from the bottom: the
+// columns of Q G, formed by eigvec_column). Deflation from the bottom: the
 // block [l, m] with m = N-1 .. 1 and l the first row below the last
 // negligible sub-diagonal entry; each step chases the bulge of one
 // Wilkinson-shifted QR step down the block with Givens rotations
@@ -283,25 +288,46 @@ __device__ __forceinline__ void tridiag_qr(Herm<N> &M) {
             }
         }
     }
-    // eigenvectors: Q <- Q G
+}
+
+// Eigenvector n of H: column n of Q G = H_0 (H_1 (... H_{N-3} (diag(delta) G e_n))),
+// the reflectors applied last to first as x <- x - 2 u (u^H x).
+template <int N>
+__device__ __forceinline__ void eigvec_column(const Herm<N> &M, int n, float (&xr)[N], float (&xi)[N]) {
 #pragma unroll
     for (int r = 0; r < N; ++r) {
-        float vr[N], vi[N];
+        xr[r] = M.sr[r] * M.g[r][n];
+        xi[r] = M.si[r] * M.g[r][n];
+    }
 #pragma unroll
-        for (int n = 0; n < N; ++n) {
-            float sr = 0.f, si = 0.f;
+    for (int k = N - 3; k >= 0; --k) {
+        float tr = 0.f, ti = 0.f;   // u^H x
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-                sr = fmaf(M.qr[r][k], M.g[k][n], sr);
-                si = fmaf(M.qi[r][k], M.g[k][n], si);
-            }
-            vr[n] = sr;
-            vi[n] = si;
+        for (int j = k + 1; j < N; ++j) {
+            tr = fmaf(M.ur[k][j], xr[j], fmaf(M.ui[k][j], xi[j], tr));
+            ti = fmaf(M.ur[k][j], xi[j], fmaf(-M.ui[k][j], xr[j], ti));
         }
+        tr *= 2.f;
+        ti *= 2.f;
 #pragma unroll
-        for (int n = 0; n < N; ++n) {
-            M.qr[r][n] = vr[n];
-            M.qi[r][n] = vi[n];
+        for (int j = k + 1; j < N; ++j) {
+            xr[j] = fmaf(-M.ur[k][j], tr, fmaf(M.ui[k][j], ti, xr[j]));
+            xi[j] = fmaf(-M.ur[k][j], ti, fmaf(-M.ui[k][j], tr, xi[j]));
+        }
+    }
+}
+
+// All eigenvectors into M.qr / M.qi (column n = eigenvector of d[n]).
+template <int N>
+__device__ __forceinline__ void eigenvectors(Herm<N> &M) {
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        float xr[N], xi[N];
+        eigvec_column<N>(M, n, xr, xi);
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            M.qr[r][n] = xr[r];
+            M.qi[r][n] = xi[r];
         }
     }
 }
