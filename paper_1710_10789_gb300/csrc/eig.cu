@@ -8,9 +8,9 @@
 // reduces it to real tridiagonal form by Householder reflections and
 // diagonalises that by implicit-shift QR, with H, the reflectors, the
 // accumulated rotations and the tridiagonal in registers (all indices
-// compile-time after unrolling), forms each eigenvector by applying the
-// reflectors to a column of the rotations, then sorts the eigenpairs with a
-// transposition network and stores eps_n and |V_sn|^2.
+// compile-time after unrolling), ranks the eigenvalues, and stores each
+// eigenvalue and the squared moduli of its eigenvector (formed by applying the
+// reflectors to a column of the rotations) at its place in ascending order.
 #include "eig_common.cuh"
 
 namespace tetra {
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
     Herm<N> M;
     {
         Mat<N> H;   // upper triangle of H(k)
-        build_h<N>(H, s_on, s_hop, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
+        build_h<N>(H, s_on, s_hop, s_R, A.n_R, x, y, z, grid3(A.n1, A.n2, A.n3));
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -45,72 +45,61 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
                 M.ai[i][j] = (i == j) ? 0.f : -H.hi[j][i];
             }
     }
-    float ev[N];
-    float W[N][N];   // W[n][s] = |V_sn|^2
+    float *eo = A.eps + p * A.eps_stride;
+    WT *wo = static_cast<WT *>(A.w) + p * A.w_stride;
     if constexpr (N == 1) {
-        ev[0] = M.ar[0][0];
-        W[0][0] = 1.f;
+        eo[0] = M.ar[0][0];
+        wo[0] = from_f32<WT>(1.f);
+        return;
     } else {
         householder_tridiag<N>(M);
         tridiag_qr<N>(M);
+        // place of each eigenpair in ascending order; equal eigenvalues keep
+        // their column order (a NaN counts as +inf, so the places stay a
+        // permutation whatever the input)
+        float key[N];
+        int rank[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) key[j] = isnan(M.d[j]) ? INFINITY : M.d[j];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            int r = 0;
+#pragma unroll
+            for (int i = 0; i < N; ++i) r += (key[i] < key[j]) || (key[i] == key[j] && i < j);
+            rank[j] = r;
+        }
+#pragma unroll
+        for (int j = 0; j < N; ++j) eo[rank[j]] = M.d[j];
+        // weights |V_sn|^2 of eigenvector n, stored as band row rank[n]: whole
+        // 16-byte vectors when a row fills them (the point strides are
+        // multiples of 16 bytes), scalars otherwise
+        constexpr int VEC = 16 / sizeof(WT);
 #pragma unroll
         for (int n = 0; n < N; ++n) {
-            ev[n] = M.d[n];
-            float vr[N], vi[N];
+            float vr[N], vi[N], b[N];
             eigvec_column<N>(M, n, vr, vi);
 #pragma unroll
-            for (int s = 0; s < N; ++s) W[n][s] = vr[s] * vr[s] + vi[s] * vi[s];
-        }
-    }
-    // eigenvalues and weights, sorted ascending (odd-even transposition network)
+            for (int s = 0; s < N; ++s) b[s] = vr[s] * vr[s] + vi[s] * vi[s];
+            if (A.n_orb_out < N) {
+                // projection on the first n_orb_out orbitals only
 #pragma unroll
-    for (int round = 0; round < N; ++round)
+                for (int s = 0; s < N; ++s)
+                    if (s < A.n_orb_out) wo[rank[n] * A.n_orb_out + s] = from_f32<WT>(b[s]);
+            } else if constexpr (N % VEC == 0) {
+                uint4 *row = reinterpret_cast<uint4 *>(wo + rank[n] * N);
 #pragma unroll
-        for (int a = (round & 1); a + 1 < N; a += 2) {
-            const bool sw = ev[a + 1] < ev[a];
-            const float lo = sw ? ev[a + 1] : ev[a], hi = sw ? ev[a] : ev[a + 1];
-            ev[a] = lo; ev[a + 1] = hi;
+                for (int v = 0; v < N / VEC; ++v) {
+                    uint4 q;
+                    WT *e = reinterpret_cast<WT *>(&q);
 #pragma unroll
-            for (int s = 0; s < N; ++s) {
-                const float u = W[a][s], v = W[a + 1][s];
-                W[a][s] = sw ? v : u;
-                W[a + 1][s] = sw ? u : v;
+                    for (int j = 0; j < VEC; ++j) e[j] = from_f32<WT>(b[v * VEC + j]);
+                    row[v] = q;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < N; ++s) wo[rank[n] * N + s] = from_f32<WT>(b[s]);
             }
         }
-    // Stores: 16-byte vectors when a point's values fill whole vectors (the
-    // layout's point strides are multiples of 16 bytes), scalars otherwise.
-    float *eo = A.eps + p * A.eps_stride;
-    if constexpr (N % 4 == 0) {
-#pragma unroll
-        for (int n = 0; n < N; n += 4)
-            *reinterpret_cast<float4 *>(eo + n) = make_float4(ev[n], ev[n + 1], ev[n + 2], ev[n + 3]);
-    } else {
-#pragma unroll
-        for (int n = 0; n < N; ++n) eo[n] = ev[n];
-    }
-    WT *wo = static_cast<WT *>(A.w) + p * A.w_stride;
-    constexpr int VEC = 16 / sizeof(WT);
-    if (A.n_orb_out < N) {
-        // projection on the first n_orb_out orbitals only: w[n][s], s < n_orb_out
-#pragma unroll
-        for (int n = 0; n < N; ++n)
-#pragma unroll
-            for (int s = 0; s < N; ++s)
-                if (s < A.n_orb_out) wo[n * A.n_orb_out + s] = from_f32<WT>(W[n][s]);
-    } else if constexpr ((N * N) % VEC == 0) {
-#pragma unroll
-        for (int v = 0; v < N * N / VEC; ++v) {
-            uint4 q;
-            WT *e = reinterpret_cast<WT *>(&q);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) e[j] = from_f32<WT>(W[(v * VEC + j) / N][(v * VEC + j) % N]);
-            reinterpret_cast<uint4 *>(wo)[v] = q;
-        }
-    } else {
-#pragma unroll
-        for (int n = 0; n < N; ++n)
-#pragma unroll
-            for (int s = 0; s < N; ++s) wo[n * N + s] = from_f32<WT>(W[n][s]);
     }
 }
 

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
     stage_model<N>(A.params, A.R, A.n_R, A.n1, A.n2, A.n3, s_on, s_hop, s_R);
     __syncthreads();
     const long nk = (long)A.n1 * A.n2 * A.n3;
+    const Grid3 g3 = grid3(A.n1, A.n2, A.n3);
     // outputs owned by this thread: o = tid, tid + kBT, ... (accumulated in acc[o])
     for (int o = tid; o < A.n_out; o += kBT) acc[o] = 0.0;
     float *V = Vs + tid * NN2, *In = Is + tid * NN2, *X = Xs + tid * NN2, *ph = Ph + tid * 2 * A.n_R;
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
             Herm<N> M;
             {
                 Mat<N> H;
-                build_h<N>(H, s_on, s_hop, s_R, A.n_R, x, y, z, A.n1, A.n2, A.n3);
+                build_h<N>(H, s_on, s_hop, s_R, A.n_R, x, y, z, g3);
 #pragma unroll
                 for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
                     In[2 * (i * N + j)] = Qr[i][j] + Qr[j][i];
                     In[2 * (i * N + j) + 1] = Qi[i][j] - Qi[j][i];
                 }
-            for (int r = 0; r < A.n_R; ++r) phase(s_R + 3 * r, x, y, z, A.n1, A.n2, A.n3, ph[2 * r + 1], ph[2 * r]);
+            for (int r = 0; r < A.n_R; ++r) phase(s_R + 3 * r, x, y, z, g3, ph[2 * r + 1], ph[2 * r]);
         } else {
             for (int i = 0; i < NN2; ++i) In[i] = 0.f;
             for (int r = 0; r < 2 * A.n_R; ++r) ph[r] = 0.f;

@@ -33,15 +33,34 @@ __device__ __forceinline__ int reduce_mod(int a, int n) {
     return m < 0 ? m + n : m;
 }
 
+// (a b) mod n for 0 <= a, b < n <= 4096: the product is below 2^24, exact in
+// FP32, so the quotient taken from a float product is off by at most one and
+// the remainder is corrected into [0, n).
+__device__ __forceinline__ int mulmod(int a, int b, int n, float inv_n) {
+    const int ab = a * b;
+    int m = ab - n * __float2int_rz(__int2float_rn(ab) * inv_n);
+    m = m < 0 ? m + n : m;
+    return m >= n ? m - n : m;
+}
+
+// Grid extents and their reciprocals, for the phases.
+struct Grid3 {
+    int n1, n2, n3;
+    float i1, i2, i3;
+};
+__device__ __forceinline__ Grid3 grid3(int n1, int n2, int n3) {
+    return Grid3{n1, n2, n3, 1.f / n1, 1.f / n2, 1.f / n3};
+}
+
 // e^{i k.R} at grid point (x, y, z) for R given reduced mod (n1, n2, n3):
 // 2 pi k.R is reduced exactly with integer arithmetic, m_i = (x_i R_i) mod n_i,
 // before the single-precision sin/cos.
-__device__ __forceinline__ void phase(const int *R, int x, int y, int z, int n1, int n2, int n3,
-                                      float &sn, float &cs) {
-    const int m0 = (x * R[0]) % n1;
-    const int m1 = (y * R[1]) % n2;
-    const int m2 = (z * R[2]) % n3;
-    const float frac = (float)m0 / n1 + (float)m1 / n2 + (float)m2 / n3;
+__device__ __forceinline__ void phase(const int *R, int x, int y, int z, const Grid3 &g, float &sn,
+                                      float &cs) {
+    const int m0 = mulmod(x, R[0], g.n1, g.i1);
+    const int m1 = mulmod(y, R[1], g.n2, g.i2);
+    const int m2 = mulmod(z, R[2], g.n3, g.i3);
+    const float frac = (float)m0 * g.i1 + (float)m1 * g.i2 + (float)m2 * g.i3;
     sincospif(2.0f * frac, &sn, &cs);
 }
 
@@ -80,15 +99,15 @@ __device__ __forceinline__ void stage_model(const float *params, const int *R, i
 // D = t_ij - t_ji.
 template <int N>
 __device__ __forceinline__ void build_h(Mat<N> &M, const float *s_on, const float4 *s_hop,
-                                        const int *s_R, int n_R, int x, int y, int z, int n1,
-                                        int n2, int n3) {
+                                        const int *s_R, int n_R, int x, int y, int z,
+                                        const Grid3 &g) {
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
         for (int j = i; j < N; ++j) { M.hr[i][j] = (i == j) ? s_on[i] : 0.f; M.hi[i][j] = 0.f; }
     for (int r = 0; r < n_R; ++r) {
         float sn, cs;
-        phase(s_R + 3 * r, x, y, z, n1, n2, n3, sn, cs);
+        phase(s_R + 3 * r, x, y, z, g, sn, cs);
         const float4 *h = s_hop + r * n_upper<N>();
 #pragma unroll
         for (int i = 0, q = 0; i < N; ++i)
