@@ -466,31 +466,35 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     }
 
     // Work sequence of this CTA: item k -> (model, box). Single model: boxes
-    // blockIdx.x, blockIdx.x + gridDim.x, ... Batched: thread 0 claims the next
-    // global item (models in order, boxes within a model) from a counter when
-    // it issues the item's TMA loads, so every CTA stays busy until the batch
-    // is done; s_work holds the claimed items of steps k .. k+2.
-    __shared__ int s_work[4];
+    // blockIdx.x, blockIdx.x + gridDim.x, ... Batched: thread 0 claims global
+    // items (models in order, boxes within a model) from a counter, two steps
+    // ahead, so every CTA stays busy until the batch is done; the claim for
+    // step k+2 is issued when step k starts and decoded when step k ends (its
+    // latency hidden behind the box), and s_wm / s_wb hold the decoded
+    // (model, box) of steps k .. k+2 (model -1: no more work).
+    __shared__ int s_wm[4], s_wb[4];
+    int claim_m = 0;   // thread 0: model of its last claim (claims only grow)
+    auto store_claim = [&](int k, int g) {   // thread 0 only
+        if (g >= B.total_work) {
+            s_wm[k & 3] = -1;
+            return;
+        }
+        while (claim_m + 1 < B.n_models && B.m[claim_m + 1].box_base <= g) ++claim_m;
+        s_wm[k & 3] = claim_m;
+        s_wb[k & 3] = g - B.m[claim_m].box_base;
+    };
     auto work = [&](int k, int &mi, int &box) -> bool {
         if (MAXM == 1) {
             mi = 0;
             box = blockIdx.x + k * gridDim.x;
             return box < B.m[0].n_boxes;
         }
-        const int g = s_work[k & 3];
-        if (g < 0) return false;
-        int m = 0;
-        while (m + 1 < B.n_models && B.m[m + 1].box_base <= g) ++m;
-        mi = m;
-        box = g - B.m[m].box_base;
-        return true;
+        mi = s_wm[k & 3];
+        box = s_wb[k & 3];
+        return mi >= 0;
     };
-    // energies of work item k into energy stage stg (claims the item in a batch)
+    // energies of work item k (already claimed) into energy stage stg
     auto issue_e = [&](int k, int stg) {   // thread 0 only
-        if (MAXM > 1) {
-            const int g = atomicAdd(A.queue, 1);
-            s_work[k & 3] = g < B.total_work ? g : -1;
-        }
         int mi, box;
         if (!work(k, mi, box)) return;
         const ModelP &Mk = B.m[mi];
@@ -512,10 +516,15 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     __syncthreads();
     // prologue: energies of the first two work items, weights of the first
     if (tid == 0) {
+        if (MAXM > 1) {
+            store_claim(0, atomicAdd(A.queue, 1));
+            store_claim(1, atomicAdd(A.queue, 1));
+        }
         issue_e(0, 0);
         issue_e(1, 1);
         issue_w(0);
     }
+    int g_next = 0;   // thread 0: the claim in flight (step k+2)
     __syncthreads();
 
     const int PX = A.BX + 1, PY = A.BY + 1;
@@ -605,6 +614,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     for (int k = 0;; ++k) {
         int mi, box;
         if (!work(k, mi, box)) break;
+        if (MAXM > 1 && tid == 0) g_next = atomicAdd(A.queue, 1);
         const ModelP &M = B.m[mi];
         if (mi != cur) {
             // switch model: flush the previous one, reset the tile, cache the energy grid
@@ -1019,6 +1029,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         // refill: energies of work item k+2 into this energy stage, weights of k+1
         if (tid == 0) {
             fence_proxy_async_smem();
+            if (MAXM > 1) store_claim(k + 2, g_next);
             issue_e(k + 2, st);
             issue_w(k + 1);
         }
