@@ -6,9 +6,9 @@
 // have the point as a corner (in a fixed order, so the float sums are
 // deterministic without atomics), re-sorts each one and, for every bin the
 // tetrahedron overlaps, evaluates the corner weights of Sec. II.C together
-// with their derivatives with respect to the four sorted corner energies by
-// forward-mode dual numbers (value + 4 tangents) carried through the paper's
-// formulas. The point then collects
+// with their derivatives with respect to the energy of the thread's own corner
+// (forward mode, one tangent, carried through the paper's formulas with the
+// reciprocal energy differences formed once per tetrahedron). The point then collects
 //   dL/db_{p,s}  += g_si dW_l(p)/dE_i
 //   dL/deps_p    += sum_s g_si sum_l b_{l,s} dW_l/de_{l(p)}      (bin averages)
 #include "tetra_internal.cuh"
@@ -19,68 +19,80 @@ namespace {
 
 constexpr int kBwdThreads = 128;
 
-// value and derivatives with respect to the 4 sorted corner energies
-struct D4 {
-    float v, d[4];
+// A value and its derivative along one direction: the energy of the sorted
+// corner that holds the thread's own grid point (forward-mode AD with one
+// tangent; the other three corner energies are constants).
+struct F1 {
+    float v, d;
 };
-__device__ __forceinline__ D4 dconst(float v) { D4 r; r.v = v; r.d[0] = r.d[1] = r.d[2] = r.d[3] = 0.f; return r; }
-__device__ __forceinline__ D4 operator+(const D4 &a, const D4 &b) { D4 r; r.v = a.v + b.v;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
-__device__ __forceinline__ D4 operator-(const D4 &a, const D4 &b) { D4 r; r.v = a.v - b.v;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
-__device__ __forceinline__ D4 operator*(const D4 &a, const D4 &b) { D4 r; r.v = a.v * b.v;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
-__device__ __forceinline__ D4 operator*(float s, const D4 &a) { D4 r; r.v = s * a.v;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r.d[k] = s * a.d[k]; return r; }
-__device__ __forceinline__ D4 operator/(const D4 &a, const D4 &b) {
-    const float ib = 1.0f / b.v;
-    D4 r; r.v = a.v * ib;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
-    return r;
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1{a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1{a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1{a.v * b.v, fmaf(a.d, b.v, a.v * b.d)}; }
+__device__ __forceinline__ F1 operator*(float s, F1 a) { return F1{s * a.v, s * a.d}; }
+__device__ __forceinline__ F1 operator-(float s, F1 a) { return F1{s - a.v, -a.d}; }
+
+// Per-tetrahedron constants: the sorted corner energies with their tangents
+// (1 for the differentiated corner, 0 otherwise) and the reciprocal energy
+// differences 1/E_ab with theirs (d(1/x) = -dx/x^2). A difference that is
+// not positive gets 0: no region that reads it is ever entered then (the
+// regions are half-open, so every executed branch has positive denominators).
+struct TetD {
+    F1 e1, e2, e3, e4;
+    F1 r21, r31, r41, r32, r42, r43;
+};
+__device__ __forceinline__ F1 rcp_diff(F1 a, F1 b) {   // 1 / (a - b)
+    const float x = a.v - b.v;
+    const float r = x > 0.f ? 1.0f / x : 0.f;
+    return F1{r, -(a.d - b.d) * r * r};
+}
+__device__ __forceinline__ void tetd_setup(TetD &T, const float e[4], int r_my) {
+    T.e1 = F1{e[0], r_my == 0 ? 1.f : 0.f};
+    T.e2 = F1{e[1], r_my == 1 ? 1.f : 0.f};
+    T.e3 = F1{e[2], r_my == 2 ? 1.f : 0.f};
+    T.e4 = F1{e[3], r_my == 3 ? 1.f : 0.f};
+    T.r21 = rcp_diff(T.e2, T.e1); T.r31 = rcp_diff(T.e3, T.e1); T.r41 = rcp_diff(T.e4, T.e1);
+    T.r32 = rcp_diff(T.e3, T.e2); T.r42 = rcp_diff(T.e4, T.e2); T.r43 = rcp_diff(T.e4, T.e3);
 }
 
-// Corner weights w_l(E) (Sec. II.C, all five cases) with derivatives with
-// respect to the sorted corner energies; f = V_T/(4 V_G). Regions are taken
-// half-open as in the forward kernel.
-__device__ void weights_dual(const float e[4], float E, float f, D4 w[4]) {
-    D4 E1 = dconst(e[0]), E2 = dconst(e[1]), E3 = dconst(e[2]), E4 = dconst(e[3]);
-    E1.d[0] = 1.f; E2.d[1] = 1.f; E3.d[2] = 1.f; E4.d[3] = 1.f;
-    const D4 EE = dconst(E);
-    if (E <= e[0]) {
-        for (int l = 0; l < 4; ++l) w[l] = dconst(0.f);
-    } else if (E >= e[3]) {
-        for (int l = 0; l < 4; ++l) w[l] = dconst(f);
-    } else if (E <= e[1]) {
-        const D4 E21 = E2 - E1, E31 = E3 - E1, E41 = E4 - E1, x = EE - E1;
-        const D4 C = f * (x * x * x) / (E21 * E31 * E41);
-        const D4 S = dconst(1.f) / E21 + dconst(1.f) / E31 + dconst(1.f) / E41;
-        w[0] = C * (dconst(4.f) - x * S);
-        w[1] = C * x / E21;
-        w[2] = C * x / E31;
-        w[3] = C * x / E41;
-    } else if (E <= e[2]) {
-        const D4 E31 = E3 - E1, E41 = E4 - E1, E32 = E3 - E2, E42 = E4 - E2;
-        const D4 a = EE - E1, bq = EE - E2, c = E3 - EE, dd = E4 - EE;
-        const D4 C1 = f * (a * a) / (E31 * E41);
-        const D4 C2 = f * (a * bq * c) / (E31 * E32 * E41);
-        const D4 C3 = f * (bq * bq * dd) / (E32 * E41 * E42);
-        w[0] = C1 + (C1 + C2) * c / E31 + (C1 + C2 + C3) * dd / E41;
-        w[1] = C1 + C2 + C3 + (C2 + C3) * c / E32 + C3 * dd / E42;
-        w[2] = (C1 + C2) * a / E31 + (C2 + C3) * bq / E32;
-        w[3] = (C1 + C2 + C3) * a / E41 + C3 * bq / E42;
+// Corner weights w_l(E) (Sec. II.C, all five cases) with their derivatives
+// along the tangent of T; f = V_T/(4 V_G). Regions are taken half-open as in
+// the forward kernel.
+__device__ __forceinline__ void weights_tan(const TetD &T, float E, float f, F1 w[4]) {
+    if (E <= T.e1.v) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) w[l] = F1{0.f, 0.f};
+    } else if (E >= T.e4.v) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) w[l] = F1{f, 0.f};
+    } else if (E <= T.e2.v) {
+        const F1 x = E - T.e1;
+        const F1 C = f * (((x * x) * x) * ((T.r21 * T.r31) * T.r41));
+        const F1 S = T.r21 + T.r31 + T.r41;
+        const F1 Cx = C * x;
+        w[0] = C * (4.f - x * S);
+        w[1] = Cx * T.r21;
+        w[2] = Cx * T.r31;
+        w[3] = Cx * T.r41;
+    } else if (E <= T.e3.v) {
+        const F1 a = E - T.e1, bq = E - T.e2, c = T.e3 - F1{E, 0.f}, dd = T.e4 - F1{E, 0.f};
+        const F1 r3141 = T.r31 * T.r41;
+        const F1 C1 = f * ((a * a) * r3141);
+        const F1 C2 = f * (((a * bq) * c) * (r3141 * T.r32));
+        const F1 C3 = f * (((bq * bq) * dd) * ((T.r32 * T.r41) * T.r42));
+        const F1 C12 = C1 + C2, C23 = C2 + C3, C123 = C12 + C3;
+        w[0] = C1 + (C12 * c) * T.r31 + (C123 * dd) * T.r41;
+        w[1] = C123 + (C23 * c) * T.r32 + (C3 * dd) * T.r42;
+        w[2] = (C12 * a) * T.r31 + (C23 * bq) * T.r32;
+        w[3] = (C123 * a) * T.r41 + (C3 * bq) * T.r42;
     } else {
-        const D4 E41 = E4 - E1, E42 = E4 - E2, E43 = E4 - E3, y = E4 - EE;
-        const D4 C = f * (y * y * y) / (E41 * E42 * E43);
-        const D4 S = dconst(1.f) / E41 + dconst(1.f) / E42 + dconst(1.f) / E43;
-        w[0] = dconst(f) - C * y / E41;
-        w[1] = dconst(f) - C * y / E42;
-        w[2] = dconst(f) - C * y / E43;
-        w[3] = dconst(f) - C * (dconst(4.f) - S * y);
+        const F1 y = T.e4 - F1{E, 0.f};
+        const F1 C = f * (((y * y) * y) * ((T.r41 * T.r42) * T.r43));
+        const F1 S = T.r41 + T.r42 + T.r43;
+        const F1 Cy = C * y;
+        w[0] = f - Cy * T.r41;
+        w[1] = f - Cy * T.r42;
+        w[2] = f - Cy * T.r43;
+        w[3] = f - C * (4.f - S * y);
     }
 }
 
@@ -173,21 +185,30 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
 #pragma unroll
                 for (int s = 0; s < NORB; ++s)
                     b[r][s] = (s < A.n_orb) ? to_f32<WT>(W[(long)pt[slot[r]] * A.w_stride + (long)n * A.n_orb + s]) : 0.f;
-            D4 wl[4], wu[4];
-            weights_dual(e, A.edges[lo], A.f, wl);
+            TetD TD;
+            tetd_setup(TD, e, r_my);
+            // the own corner's weight, selected without a runtime register index
+            auto own = [&](const F1 (&w)[4]) {
+                return r_my == 0 ? w[0].v : r_my == 1 ? w[1].v : r_my == 2 ? w[2].v : w[3].v;
+            };
+            F1 wl[4], wu[4];
+            weights_tan(TD, A.edges[lo], A.f, wl);
             for (int i = lo; i <= hi; ++i) {
-                weights_dual(e, A.edges[i + 1], A.f, wu);
+                weights_tan(TD, A.edges[i + 1], A.f, wu);
                 const float iw = 1.0f / (A.edges[i + 1] - A.edges[i]);
                 // dW_l/dE-bin for this corner, and sum_l b_l dW_l/de_{r_my}
-                const float dWmy = (wu[r_my].v - wl[r_my].v) * iw;
+                const float dWmy = (own(wu) - own(wl)) * iw;
+                float dw[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) dw[r] = wu[r].d - wl[r].d;
 #pragma unroll
                 for (int s = 0; s < NORB; ++s) {
                     if (s >= A.n_orb) continue;
-                    const float g = A.grad_dos[(long)s * A.n_bins + i];
+                    const float g = __ldg(A.grad_dos + (long)s * A.n_bins + i);
                     acc_w[s] = fmaf(g, dWmy, acc_w[s]);
                     float de = 0.f;
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) de = fmaf(b[r][s], wu[r].d[r_my] - wl[r].d[r_my], de);
+                    for (int r = 0; r < 4; ++r) de = fmaf(b[r][s], dw[r], de);
                     acc_e = fmaf(g * iw, de, acc_e);
                 }
 #pragma unroll

@@ -11,8 +11,9 @@
 // + sum_r [t_r e^{ik.R_r} + h.c.]:
 //   dL/d onsite_i = Re sum_k Q_ii,
 //   dL/d Re t_r   = Re sum_k e^{ik.R_r} (Q + Q^H),   dL/d Im t_r = -Im (same).
-// Each persistent block accumulates its k-points in a fixed order; a second
-// kernel adds the block partials in FP64 in block order (deterministic).
+// Each persistent block accumulates its k-points in a fixed order (FP32 over
+// one block step of 64 k-points, FP64 across steps); a second kernel adds the
+// block partials in FP64 in block order (deterministic).
 #include "eig_common.cuh"
 
 namespace tetra {
@@ -82,16 +83,17 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
             } else {
                 householder_tridiag<N>(M);
                 tridiag_qr<N>(M);
-                eigenvectors<N>(M);
 #pragma unroll
-                for (int j = 0; j < N; ++j) lam[j] = M.d[j];
+                for (int j = 0; j < N; ++j) {
+                    lam[j] = M.d[j];
+                    float vr[N], vi[N];
+                    eigvec_column<N>(M, j, vr, vi);
 #pragma unroll
-                for (int s = 0; s < N; ++s)
-#pragma unroll
-                    for (int j = 0; j < N; ++j) {
-                        V[2 * (s * N + j)] = M.qr[s][j];
-                        V[2 * (s * N + j) + 1] = M.qi[s][j];
+                    for (int s = 0; s < N; ++s) {
+                        V[2 * (s * N + j)] = vr[s];
+                        V[2 * (s * N + j) + 1] = vi[s];
                     }
+                }
             }
             // sorted band index of each eigenvector column (ties keep column
             // order, as the forward's stable transposition sort does)
@@ -107,37 +109,44 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
             float ge[N];
 #pragma unroll
             for (int j = 0; j < N; ++j) ge[j] = A.geps[p * A.eps_stride + rank[j]];
-            // inner = diag(geps) + 2 B, B_mn = F_nm A_nm, A_nm = sum_s gw_ns conj(V_sn) V_sm
+            // S = inner + inner^H with inner = diag(geps) + 2 B, B_mn = F_nm A_nm,
+            // A_nm = sum_s gw_ns conj(V_sn) V_sm; F is antisymmetric, so
+            // S_nn = 2 geps_n and, for m != n,
+            // S_mn = 2 F_nm sum_s (gw_ns - gw_ms) conj(V_sn) V_sm,  S_nm = conj(S_mn).
+            // Then Q + Q^H = conj(V) S V^T, a Hermitian product: only i <= j formed.
+            // gw of band n (column order) and orbital s, staged in X until Y
+            // overwrites it
 #pragma unroll
             for (int n = 0; n < N; ++n) {
                 const float *g = A.gw + p * A.w_stride + (long)rank[n] * N;
-                float gws[N];
 #pragma unroll
-                for (int s = 0; s < N; ++s) gws[s] = g[s];
+                for (int s = 0; s < N; ++s) X[n * N + s] = g[s];
+            }
 #pragma unroll
-                for (int m = 0; m < N; ++m) {
+            for (int n = 0; n < N; ++n) {
+                In[2 * (n * N + n)] = 2.f * ge[n];
+                In[2 * (n * N + n) + 1] = 0.f;
+#pragma unroll
+                for (int m = 0; m < n; ++m) {
                     float ar = 0.f, ai = 0.f;
-                    if (m != n) {
 #pragma unroll
-                        for (int s = 0; s < N; ++s) {
-                            const float vnr = V[2 * (s * N + n)], vni = V[2 * (s * N + n) + 1];
-                            const float vmr = V[2 * (s * N + m)], vmi = V[2 * (s * N + m) + 1];
-                            // conj(V_sn) V_sm
-                            ar = fmaf(gws[s], vnr * vmr + vni * vmi, ar);
-                            ai = fmaf(gws[s], vnr * vmi - vni * vmr, ai);
-                        }
-                        const double d = (double)lam[n] - (double)lam[m];
-                        const float F = (float)(d / (d * d + kEta * kEta));
-                        ar *= 2.f * F;
-                        ai *= 2.f * F;
-                    } else {
-                        ar = ge[n];
+                    for (int s = 0; s < N; ++s) {
+                        const float vnr = V[2 * (s * N + n)], vni = V[2 * (s * N + n) + 1];
+                        const float vmr = V[2 * (s * N + m)], vmi = V[2 * (s * N + m) + 1];
+                        const float dg = X[n * N + s] - X[m * N + s];
+                        // conj(V_sn) V_sm
+                        ar = fmaf(dg, vnr * vmr + vni * vmi, ar);
+                        ai = fmaf(dg, vnr * vmi - vni * vmr, ai);
                     }
-                    In[2 * (m * N + n)] = ar;   // inner_mn
-                    In[2 * (m * N + n) + 1] = ai;
+                    const double d = (double)lam[n] - (double)lam[m];
+                    const float F2 = 2.f * (float)(d / (d * d + kEta * kEta));
+                    In[2 * (m * N + n)] = F2 * ar;   // S_mn
+                    In[2 * (m * N + n) + 1] = F2 * ai;
+                    In[2 * (n * N + m)] = F2 * ar;   // S_nm = conj(S_mn)
+                    In[2 * (n * N + m) + 1] = -F2 * ai;
                 }
             }
-            // X = inner V^T : X_mj = sum_n inner_mn V_jn
+            // Y = S V^T : Y_mj = sum_n S_mn V_jn
 #pragma unroll
             for (int m = 0; m < N; ++m)
 #pragma unroll
@@ -147,35 +156,31 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
                     for (int n = 0; n < N; ++n) {
                         const float ir = In[2 * (m * N + n)], ii = In[2 * (m * N + n) + 1];
                         const float vr = V[2 * (j * N + n)], vi = V[2 * (j * N + n) + 1];
-                        xr += ir * vr - ii * vi;
-                        xi += ir * vi + ii * vr;
+                        xr = fmaf(ir, vr, fmaf(-ii, vi, xr));
+                        xi = fmaf(ir, vi, fmaf(ii, vr, xi));
                     }
                     X[2 * (m * N + j)] = xr;
                     X[2 * (m * N + j) + 1] = xi;
                 }
-            // Q_ij = sum_m conj(V_im) X_mj ; store Q + Q^H in In
-            float Qr[N][N], Qi[N][N];
+            // Z = conj(V) Y = Q + Q^H into In (i <= j, mirrored; real diagonal)
 #pragma unroll
             for (int i = 0; i < N; ++i)
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    float qr = 0.f, qi = 0.f;
+                for (int j = i; j < N; ++j) {
+                    float zr = 0.f, zi = 0.f;
 #pragma unroll
                     for (int m = 0; m < N; ++m) {
                         const float vr = V[2 * (i * N + m)], vi = -V[2 * (i * N + m) + 1];
-                        const float xr = X[2 * (m * N + j)], xi = X[2 * (m * N + j) + 1];
-                        qr += vr * xr - vi * xi;
-                        qi += vr * xi + vi * xr;
+                        const float yr = X[2 * (m * N + j)], yi = X[2 * (m * N + j) + 1];
+                        zr = fmaf(vr, yr, fmaf(-vi, yi, zr));
+                        zi = fmaf(vr, yi, fmaf(vi, yr, zi));
                     }
-                    Qr[i][j] = qr;
-                    Qi[i][j] = qi;
-                }
-#pragma unroll
-            for (int i = 0; i < N; ++i)
-#pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    In[2 * (i * N + j)] = Qr[i][j] + Qr[j][i];
-                    In[2 * (i * N + j) + 1] = Qi[i][j] - Qi[j][i];
+                    In[2 * (i * N + j)] = zr;
+                    In[2 * (i * N + j) + 1] = (i == j) ? 0.f : zi;
+                    if (i != j) {
+                        In[2 * (j * N + i)] = zr;
+                        In[2 * (j * N + i) + 1] = -zi;
+                    }
                 }
             for (int r = 0; r < A.n_R; ++r) phase(s_R + 3 * r, x, y, z, g3, ph[2 * r + 1], ph[2 * r]);
         } else {
@@ -183,25 +188,29 @@ __global__ void __launch_bounds__(kBT) tetra_eig_bwd_kernel(const EigBwdArgs A) 
             for (int r = 0; r < 2 * A.n_R; ++r) ph[r] = 0.f;
         }
         __syncthreads();
-        // block sums over the kBT k-points, in thread order
+        // block sums over the kBT k-points, in thread order: FP32 within the
+        // block step, added to the FP64 accumulator once per step (FP64
+        // arithmetic is slow on this GPU; 64 FP32 terms keep ~1e-6 relative)
         for (int o = tid; o < A.n_out; o += kBT) {
-            double s = 0.0;
+            float s = 0.f;
             if (o < N) {
-                for (int t = 0; t < kBT; ++t) s += 0.5 * (double)Is[t * NN2 + 2 * (o * N + o)];
+                for (int t = 0; t < kBT; ++t) s += Is[t * NN2 + 2 * (o * N + o)];
+                s *= 0.5f;
             } else {
                 const int q = o - N;
                 const int half = A.n_R * N * N;
                 const bool im = q >= half;
                 const int qq = im ? q - half : q;
                 const int r = qq / (N * N), ij = qq - r * N * N;
+                // Re: c zr - sn zi; Im (negated): -(sn zr + c zi)
                 for (int t = 0; t < kBT; ++t) {
                     const float c = Ph[t * 2 * A.n_R + 2 * r], sn = Ph[t * 2 * A.n_R + 2 * r + 1];
                     const float zr = Is[t * NN2 + 2 * ij], zi = Is[t * NN2 + 2 * ij + 1];
-                    // e^{i th} (zr + i zi)
-                    s += im ? -(double)(sn * zr + c * zi) : (double)(c * zr - sn * zi);
+                    const float a = im ? -sn : c, b = im ? -c : -sn;
+                    s = fmaf(a, zr, fmaf(b, zi, s));
                 }
             }
-            acc[o] += s;
+            acc[o] += (double)s;
         }
         __syncthreads();
     }
