@@ -361,24 +361,6 @@ __device__ __forceinline__ void item_window(float e1, float e4, const float *om,
     }
 }
 
-// Orbital weights of one corner of band n, as floats.
-template <int NORB, typename WT>
-__device__ __forceinline__ void load_weights(const WT *src, int n_orb, float (&b)[NORB]) {
-    constexpr int VEC = 16 / sizeof(WT);
-    if (NORB % VEC == 0 && n_orb == NORB) {
-#pragma unroll
-        for (int v = 0; v < NORB / VEC; ++v) {
-            const uint4 q = reinterpret_cast<const uint4 *>(src)[v];
-            const WT *e = reinterpret_cast<const WT *>(&q);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) b[v * VEC + j] = to_f32<WT>(e[j]);
-        }
-    } else {
-#pragma unroll
-        for (int s = 0; s < NORB; ++s) b[s] = (s < n_orb) ? to_f32<WT>(src[s]) : 0.f;
-    }
-}
-
 // One model of a launch: grid, energy grid and where its partial sums go.
 struct ModelP {
     int n1, n2, n3, z0, z1, nbx, nby, n_boxes, n_omega;

@@ -42,7 +42,7 @@ struct TetD {
 };
 __device__ __forceinline__ F1 rcp_diff(F1 a, F1 b) {   // 1 / (a - b)
     const float x = a.v - b.v;
-    const float r = x > 0.f ? 1.0f / x : 0.f;
+    const float r = x > 0.f ? __fdividef(1.0f, x) : 0.f;
     return F1{r, -(a.d - b.d) * r * r};
 }
 __device__ __forceinline__ void tetd_setup(TetD &T, const float e[4], int r_my) {
@@ -109,10 +109,31 @@ struct BwdArgs {
     const float *edges;      // n_bins + 1
     const float *grad_dos;   // [n_orb][n_bins]
     float *geps, *gw;
+    int staged;              // grad_dos, edges and 1/widths copied to shared memory
 };
+
+// Shared-memory bytes of the staged bin data, or 0 when it does not fit the
+// budget that keeps three 128-thread blocks per SM.
+inline size_t bwd_stage_bytes(int n_orb, int n_bins) {
+    const size_t b = sizeof(float) * ((size_t)n_orb * n_bins + 2 * (size_t)n_bins + 1);
+    return b <= 64 * 1024 ? b : 0;
+}
 
 template <int NORB, typename WT>
 __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArgs A) {
+    extern __shared__ float s_bins[];   // staged: grad_dos, edges, 1/widths
+    const float *gd = A.grad_dos, *ed = A.edges, *siw = nullptr;
+    if (A.staged) {
+        const int ng = A.n_orb * A.n_bins;
+        for (int i = threadIdx.x; i < ng; i += blockDim.x) s_bins[i] = A.grad_dos[i];
+        for (int i = threadIdx.x; i <= A.n_bins; i += blockDim.x) s_bins[ng + i] = A.edges[i];
+        for (int i = threadIdx.x; i < A.n_bins; i += blockDim.x)
+            s_bins[ng + A.n_bins + 1 + i] = 1.0f / (A.edges[i + 1] - A.edges[i]);
+        __syncthreads();
+        gd = s_bins;
+        ed = s_bins + ng;
+        siw = s_bins + ng + A.n_bins + 1;
+    }
     const long P = (long)A.nx * A.ny * A.nz;
     const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (gid >= P * A.nb) return;
@@ -131,8 +152,8 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
         for (int s = 0; s < A.n_orb; ++s) gw[s] = 0.f;
         return;
     }
-    const float om0 = A.edges[0];
-    const float inv_de = (float)A.n_bins / (A.edges[A.n_bins] - om0);
+    const float om0 = ed[0];
+    const float inv_de = (float)A.n_bins / (ed[A.n_bins] - om0);
     float acc_e = 0.f;
     float acc_w[NORB];
 #pragma unroll
@@ -173,18 +194,16 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
             int hi = (int)ceilf(fminf(fmaxf((e[3] - om0) * inv_de, -2.f), (float)A.n_bins + 2.f));
             lo = min(max(lo, 0), A.n_bins);
             hi = max(min(hi, A.n_bins - 1), -1);
-            while (lo > 0 && A.edges[lo] > e[0]) --lo;
-            while (lo < A.n_bins && A.edges[lo + 1] <= e[0]) ++lo;
-            while (hi < A.n_bins - 1 && (A.edges[hi + 1] < e[3] || A.edges[hi + 1] <= e[0])) ++hi;
-            while (hi >= 0 && !(A.edges[hi] < e[3] || A.edges[hi] <= e[0])) --hi;
+            while (lo > 0 && ed[lo] > e[0]) --lo;
+            while (lo < A.n_bins && ed[lo + 1] <= e[0]) ++lo;
+            while (hi < A.n_bins - 1 && (ed[hi + 1] < e[3] || ed[hi + 1] <= e[0])) ++hi;
+            while (hi >= 0 && !(ed[hi] < e[3] || ed[hi] <= e[0])) --hi;
             if (lo > hi) continue;
             // orbital weights of the four corners, in sorted order
             float b[4][NORB];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int s = 0; s < NORB; ++s)
-                    b[r][s] = (s < A.n_orb) ? to_f32<WT>(W[(long)pt[slot[r]] * A.w_stride + (long)n * A.n_orb + s]) : 0.f;
+                load_weights<NORB, WT>(W + (long)pt[slot[r]] * A.w_stride + (long)n * A.n_orb, A.n_orb, b[r]);
             TetD TD;
             tetd_setup(TD, e, r_my);
             // the own corner's weight, selected without a runtime register index
@@ -192,10 +211,10 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
                 return r_my == 0 ? w[0].v : r_my == 1 ? w[1].v : r_my == 2 ? w[2].v : w[3].v;
             };
             F1 wl[4], wu[4];
-            weights_tan(TD, A.edges[lo], A.f, wl);
+            weights_tan(TD, ed[lo], A.f, wl);
             for (int i = lo; i <= hi; ++i) {
-                weights_tan(TD, A.edges[i + 1], A.f, wu);
-                const float iw = 1.0f / (A.edges[i + 1] - A.edges[i]);
+                weights_tan(TD, ed[i + 1], A.f, wu);
+                const float iw = siw ? siw[i] : 1.0f / (ed[i + 1] - ed[i]);
                 // dW_l/dE-bin for this corner, and sum_l b_l dW_l/de_{r_my}
                 const float dWmy = (own(wu) - own(wl)) * iw;
                 float dw[4];
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
 #pragma unroll
                 for (int s = 0; s < NORB; ++s) {
                     if (s >= A.n_orb) continue;
-                    const float g = __ldg(A.grad_dos + (long)s * A.n_bins + i);
+                    const float g = gd[(long)s * A.n_bins + i];
                     acc_w[s] = fmaf(g, dWmy, acc_w[s]);
                     float de = 0.f;
 #pragma unroll
@@ -225,12 +244,18 @@ template <int NORB>
 cudaError_t launch_bwd_n(const Plan &P, const BwdArgs &A, cudaStream_t stream) {
     const long total = (long)A.nx * A.ny * A.nz * A.nb;
     const int grid = (int)((total + kBwdThreads - 1) / kBwdThreads);
+    const size_t smem = A.staged ? bwd_stage_bytes(A.n_orb, A.n_bins) : 0;
+    auto go = [&](auto kfn) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kfn<<<grid, kBwdThreads, smem, stream>>>(A);
+        return cudaGetLastError();
+    };
     switch (P.d.weight_dtype) {
-        case TETRA_F16: tetra_dos_bwd_kernel<NORB, __half><<<grid, kBwdThreads, 0, stream>>>(A); break;
-        case TETRA_BF16: tetra_dos_bwd_kernel<NORB, __nv_bfloat16><<<grid, kBwdThreads, 0, stream>>>(A); break;
-        default: tetra_dos_bwd_kernel<NORB, float><<<grid, kBwdThreads, 0, stream>>>(A); break;
+        case TETRA_F16: return go(tetra_dos_bwd_kernel<NORB, __half>);
+        case TETRA_BF16: return go(tetra_dos_bwd_kernel<NORB, __nv_bfloat16>);
+        default: return go(tetra_dos_bwd_kernel<NORB, float>);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -248,6 +273,7 @@ tetra_status_t launch_dos_backward(const Plan &P, const float *eps, const void *
     A.eps_stride = P.eps_stride; A.w_stride = P.w_stride;
     A.f = (float)(0.25 / (6.0 * (double)P.d.n1 * (double)P.d.n2 * (double)P.d.n3));
     A.eps = eps; A.w = w; A.edges = omega; A.grad_dos = grad_dos; A.geps = grad_eps; A.gw = grad_w;
+    A.staged = bwd_stage_bytes(A.n_orb, A.n_bins) > 0;
     if (cudaMemsetAsync(ws, 0, kStatusBytes, stream) != cudaSuccess) return TETRA_ECUDA;
     cudaError_t e;
     const int no = P.d.n_orb;

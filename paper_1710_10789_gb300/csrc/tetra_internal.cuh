@@ -157,6 +157,25 @@ __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2hal
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// NORB orbital weights of one (point, band) as FP32: 16-byte loads when a
+// point's row fills whole vectors, scalars (zero beyond n_orb) otherwise.
+template <int NORB, typename WT>
+__device__ __forceinline__ void load_weights(const WT *src, int n_orb, float (&b)[NORB]) {
+    constexpr int VEC = 16 / sizeof(WT);
+    if (NORB % VEC == 0 && n_orb == NORB) {
+#pragma unroll
+        for (int v = 0; v < NORB / VEC; ++v) {
+            const uint4 q = reinterpret_cast<const uint4 *>(src)[v];
+            const WT *e = reinterpret_cast<const WT *>(&q);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) b[v * VEC + j] = to_f32<WT>(e[j]);
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < NORB; ++s) b[s] = (s < n_orb) ? to_f32<WT>(src[s]) : 0.f;
+    }
+}
+
 // ---------------------------------------------------------------- host helpers
 tetra_status_t encode_point_map(CUtensorMap *map, const void *base, CUtensorMapDataType dtype,
                                 int elem_bytes, int stride_elems, int nx, int ny, int nz,
