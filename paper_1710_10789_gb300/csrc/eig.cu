@@ -72,21 +72,40 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
         for (int j = 0; j < N; ++j) eo[rank[j]] = M.d[j];
         // weights |V_sn|^2 of eigenvector n, stored as band row rank[n]: whole
         // 16-byte vectors when a row fills them (the point strides are
-        // multiples of 16 bytes), scalars otherwise
-        constexpr int VEC = 16 / sizeof(WT);
+        // multiples of 16 bytes), scalars otherwise. The columns are formed in
+        // a loop that is not unrolled (one copy of the reflector code: the
+        // unrolled solver does not fit the instruction cache), reading G and
+        // the ranks from this thread's slice of shared memory.
+        extern __shared__ float s_g[];   // [N * N + N][blockDim.x]
+        const int ts = blockDim.x;
+        float *gs = s_g + threadIdx.x;
 #pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c < N; ++c) gs[(r * N + c) * ts] = M.g[r][c];
+#pragma unroll
+        for (int j = 0; j < N; ++j) gs[(N * N + j) * ts] = __int_as_float(rank[j]);
+        constexpr int VEC = 16 / sizeof(WT);
+#pragma unroll 1
         for (int n = 0; n < N; ++n) {
             float vr[N], vi[N], b[N];
-            eigvec_column<N>(M, n, vr, vi);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                const float g = gs[(r * N + n) * ts];
+                vr[r] = M.sr[r] * g;
+                vi[r] = M.si[r] * g;
+            }
+            apply_reflectors<N>(M, vr, vi);
+            const int rk = __float_as_int(gs[(N * N + n) * ts]);
 #pragma unroll
             for (int s = 0; s < N; ++s) b[s] = vr[s] * vr[s] + vi[s] * vi[s];
             if (A.n_orb_out < N) {
                 // projection on the first n_orb_out orbitals only
 #pragma unroll
                 for (int s = 0; s < N; ++s)
-                    if (s < A.n_orb_out) wo[rank[n] * A.n_orb_out + s] = from_f32<WT>(b[s]);
+                    if (s < A.n_orb_out) wo[rk * A.n_orb_out + s] = from_f32<WT>(b[s]);
             } else if constexpr (N % VEC == 0) {
-                uint4 *row = reinterpret_cast<uint4 *>(wo + rank[n] * N);
+                uint4 *row = reinterpret_cast<uint4 *>(wo + rk * N);
 #pragma unroll
                 for (int v = 0; v < N / VEC; ++v) {
                     uint4 q;
@@ -97,7 +116,7 @@ __global__ void __launch_bounds__(kEigThreads) tetra_eig_kernel(const EigArgs A)
                 }
             } else {
 #pragma unroll
-                for (int s = 0; s < N; ++s) wo[rank[n] * N + s] = from_f32<WT>(b[s]);
+                for (int s = 0; s < N; ++s) wo[rk * N + s] = from_f32<WT>(b[s]);
             }
         }
     }
@@ -107,12 +126,18 @@ template <int N>
 cudaError_t launch_n(const Plan &P, const EigArgs &A, cudaStream_t stream) {
     const long pts = (long)A.nx * A.ny * A.nz;
     const int grid = (int)((pts + kEigThreads - 1) / kEigThreads);
+    const size_t smem = N > 1 ? sizeof(float) * (N * N + N) * kEigThreads : 0;
+    auto go = [&](auto kfn) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kfn<<<grid, kEigThreads, smem, stream>>>(A);
+        return cudaGetLastError();
+    };
     switch (P.d.weight_dtype) {
-        case TETRA_F16: tetra_eig_kernel<N, __half><<<grid, kEigThreads, 0, stream>>>(A); break;
-        case TETRA_BF16: tetra_eig_kernel<N, __nv_bfloat16><<<grid, kEigThreads, 0, stream>>>(A); break;
-        default: tetra_eig_kernel<N, float><<<grid, kEigThreads, 0, stream>>>(A); break;
+        case TETRA_F16: return go(tetra_eig_kernel<N, __half>);
+        case TETRA_BF16: return go(tetra_eig_kernel<N, __nv_bfloat16>);
+        default: return go(tetra_eig_kernel<N, float>);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace

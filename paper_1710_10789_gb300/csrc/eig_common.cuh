@@ -309,15 +309,10 @@ __device__ __forceinline__ void tridiag_qr(Herm<N> &M) {
     }
 }
 
-// Eigenvector n of H: column n of Q G = H_0 (H_1 (... H_{N-3} (diag(delta) G e_n))),
-// the reflectors applied last to first as x <- x - 2 u (u^H x).
+// x <- H_0 (H_1 (... H_{N-3} x)): the reflectors applied last to first as
+// x <- x - 2 u (u^H x).
 template <int N>
-__device__ __forceinline__ void eigvec_column(const Herm<N> &M, int n, float (&xr)[N], float (&xi)[N]) {
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-        xr[r] = M.sr[r] * M.g[r][n];
-        xi[r] = M.si[r] * M.g[r][n];
-    }
+__device__ __forceinline__ void apply_reflectors(const Herm<N> &M, float (&xr)[N], float (&xi)[N]) {
 #pragma unroll
     for (int k = N - 3; k >= 0; --k) {
         float tr = 0.f, ti = 0.f;   // u^H x
@@ -334,6 +329,17 @@ __device__ __forceinline__ void eigvec_column(const Herm<N> &M, int n, float (&x
             xi[j] = fmaf(-M.ur[k][j], ti, fmaf(-M.ui[k][j], tr, xi[j]));
         }
     }
+}
+
+// Eigenvector n of H: column n of Q G = H_0 (H_1 (... H_{N-3} (diag(delta) G e_n))).
+template <int N>
+__device__ __forceinline__ void eigvec_column(const Herm<N> &M, int n, float (&xr)[N], float (&xi)[N]) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        xr[r] = M.sr[r] * M.g[r][n];
+        xi[r] = M.si[r] * M.g[r][n];
+    }
+    apply_reflectors<N>(M, xr, xi);
 }
 
 // All eigenvectors into M.qr / M.qi (column n = eigenvector of d[n]).
