@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--mode", default="point", choices=["point", "bin"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e and extra measurements")
+    ap.add_argument("--variant", default=None, choices=["differentiation", "paper_shape", "lindhard"],
+                    help="run one extra workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -553,6 +555,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     T.build()
+    if args.variant is not None:
+        fn = {"differentiation": differentiation_workload, "paper_shape": paper_shape_workload,
+              "lindhard": lindhard_workload}[args.variant]
+        if rank == 0:
+            print(json.dumps(fn(torch, T, args.steps, args.warmup, local)), flush=True)
+        return
     n, nw = args.grid, args.n_omega
     model = tbgen.tb_model(rank, n_orb=8)
     p_np, R_np = model_arrays(model)
