@@ -66,7 +66,7 @@ constexpr uint32_t kSmemAlign = 1024;
 // sub-partition) can use 168 registers per thread, 16 warps 128.
 template <int MODE, int NORB>
 struct Cfg {
-    static constexpr bool pairs = MODE == TETRA_POINT && NORB <= 8;
+    static constexpr bool pairs = (MODE == TETRA_POINT || MODE == TETRA_INTEGRATED) && NORB <= 8;
     static constexpr int threads = pairs ? 384 : 512;
     static constexpr int max_regs = pairs ? 168 : 128;
     static constexpr int units_per_cube = pairs ? 3 : 6;
@@ -278,11 +278,13 @@ __device__ __forceinline__ void tetp_dw(const TetP &T, float E, float d[4]) {
 }
 
 // w_l(E) for any E (Sec. II.C, all five cases), sorted corners.
+template <bool OPEN = false>
 __device__ __forceinline__ void tet_weights(const Tet &T, float E, float w[4]) {
     if (E <= T.e1) {
         w[0] = w[1] = w[2] = w[3] = 0.f;
     } else if (E >= T.e4) {
-        w[0] = w[1] = w[2] = w[3] = T.fq;
+        // saturated; OPEN: zero, the saturated part being added elsewhere
+        w[0] = w[1] = w[2] = w[3] = OPEN ? 0.f : T.fq;
     } else if (E <= T.e2) {
         const float x = E - T.e1;
         const float C = 0.25f * T.P1 * x * x * x;
@@ -800,6 +802,97 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     load_weights<NORB, WT>(Ws + (long)pa[r4] * A.w_stride + n * A.n_orb, A.n_orb, ba[r4]);
                     load_weights<NORB, WT>(Ws + (long)pb[r4] * A.w_stride + n * A.n_orb, A.n_orb, bb[r4]);
                 }
+                const float dith = item_dither((gcube * 3u + (uint32_t)pr) * (uint32_t)A.nb + (uint32_t)n);
+                if constexpr (MODE == TETRA_INTEGRATED) {
+                    // Occupation: the walk over the union window adds each
+                    // tetrahedron's weights below its own E4 (zero at and above
+                    // it); from its step, the first energy at or above its E4,
+                    // the saturated weights fq sum_l b_l enter the step tile.
+                    // Every corner weight is at most V_T/(4 V_G): the pair adds
+                    // at most 8 fq Bmax to any entry.
+                    const float qmax = bmax * 8.f * fq * 1.01f;
+                    const bool fast = qmax < (float)A.fast_cap;
+                    int loa, hia, lob, hib;
+                    item_window<MODE>(ea[0], ea[3], om, w0, wc, om0, inv_de, M.n_omega, loa, hia);
+                    item_window<MODE>(eb[0], eb[3], om, w0, wc, om0, inv_de, M.n_omega, lob, hib);
+                    const int hsa = hia + 1, hsb = hib + 1;
+                    const bool stepa = hsa < w0 + wc, stepb = hsb < w0 + wc;
+                    if (fast) {
+                        const unsigned qbnd = (unsigned)qmax + 2u;
+                        if (hi >= lo) {
+                            for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
+                            atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
+                            atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
+                        }
+                        if (stepa) atomicAdd(&blk_bound[(hsa - w0) >> 6], qbnd);
+                        if (stepb) atomicAdd(&blk_bound[(hsb - w0) >> 6], qbnd);
+                    }
+                    Tet TA, TB;
+                    tet_setup(TA, ea[0], ea[1], ea[2], ea[3], fq);
+                    tet_setup(TB, eb[0], eb[1], eb[2], eb[3], fq);
+                    float sa[NORB], sb[NORB];   // saturated contributions fq sum_l b_{l,s}
+#pragma unroll
+                    for (int s = 0; s < NORB; ++s) {
+                        sa[s] = fq * ((ba[0][s] + ba[1][s]) + (ba[2][s] + ba[3][s]));
+                        sb[s] = fq * ((bb[0][s] + bb[1][s]) + (bb[2][s] + bb[3][s]));
+                    }
+                    if (fast) {
+                        const int K = hi - lo + 1;
+                        int i = lo + ((lane * max(K, 1)) >> 5);
+                        for (int j = 0; j < K; ++j) {
+                            float wa[4], wb[4];
+                            tet_weights<true>(TA, om[i - w0], wa);
+                            tet_weights<true>(TB, om[i - w0], wb);
+                            int *col = tile + (i - w0) * TS;
+#pragma unroll
+                            for (int s = 0; s < NORB; ++s) {
+                                float acc = fmaf(ba[0][s], wa[0], dith);
+                                acc = fmaf(ba[1][s], wa[1], acc);
+                                acc = fmaf(ba[2][s], wa[2], acc);
+                                acc = fmaf(ba[3][s], wa[3], acc);
+                                acc = fmaf(bb[0][s], wb[0], acc);
+                                acc = fmaf(bb[1][s], wb[1], acc);
+                                acc = fmaf(bb[2][s], wb[2], acc);
+                                acc = fmaf(bb[3][s], wb[3], acc);
+                                atomicAdd(col + s, __float_as_int(acc + kMagic));
+                            }
+                            i = (i == hi) ? lo : i + 1;
+                        }
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            if (stepa)
+                                atomicAdd(&stile[(hsa - w0) * NORB + s], __float_as_int(sa[s] + dith + kMagic) - kMagicBits);
+                            if (stepb)
+                                atomicAdd(&stile[(hsb - w0) * NORB + s], __float_as_int(sb[s] + dith + kMagic) - kMagicBits);
+                        }
+                    } else {
+                        for (int i = lo; i <= hi; ++i) {
+                            float wa[4], wb[4];
+                            tet_weights<true>(TA, om[i - w0], wa);
+                            tet_weights<true>(TB, om[i - w0], wb);
+#pragma unroll
+                            for (int s = 0; s < NORB; ++s) {
+                                if (s >= A.n_orb) continue;
+                                float acc = fmaf(ba[0][s], wa[0], dith);
+                                acc = fmaf(ba[1][s], wa[1], acc);
+                                acc = fmaf(ba[2][s], wa[2], acc);
+                                acc = fmaf(ba[3][s], wa[3], acc);
+                                acc = fmaf(bb[0][s], wb[0], acc);
+                                acc = fmaf(bb[1][s], wb[1], acc);
+                                acc = fmaf(bb[2][s], wb[2], acc);
+                                acc = fmaf(bb[3][s], wb[3], acc);
+                                deposit_one(acc, Gc + (long)s * A.chunk_w + (i - w0), A.status);
+                            }
+                        }
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            if (s >= A.n_orb) continue;
+                            if (stepa) deposit_one(sa[s] + dith, Gsc + (long)s * A.chunk_w + (hsa - w0), A.status);
+                            if (stepb) deposit_one(sb[s] + dith, Gsc + (long)s * A.chunk_w + (hsb - w0), A.status);
+                        }
+                    }
+                    continue;
+                }
                 // bound on every |contribution| of the pair, in fixed-point units:
                 // the tetrahedron DOS is at most 3/E41 of V_T/V_G; a flat
                 // tetrahedron (E1 = E4) contributes nothing in point mode
@@ -807,7 +900,6 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 const float qb = (eb[3] > eb[0]) ? bmax * 4.f * fq * 3.1f * safe_rcp(eb[3] - eb[0]) : 0.f;
                 const float qmax = qa + qb;
                 const bool fast = qmax < (float)A.fast_cap;
-                const float dith = item_dither((gcube * 3u + (uint32_t)pr) * (uint32_t)A.nb + (uint32_t)n);
                 if (fast) {
                     const unsigned qbnd = (unsigned)qmax + 2u;
                     for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
