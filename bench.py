@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--mode", default="point", choices=["point", "bin"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e and extra measurements")
-    ap.add_argument("--variant", default=None, choices=["differentiation", "paper_shape", "lindhard"],
+    ap.add_argument("--variant", default=None, choices=["differentiation", "paper_shape", "lindhard", "near_balance"],
                     help="run one extra workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -215,6 +215,46 @@ def time_dos(torch, plan, eps, w, omega, out, steps, warmup):
     b.record(s)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / steps
+
+
+def near_balance_workload(torch, T, n, params, R, steps, warmup, local, nbins=200):
+    """The configuration with the fewest energies per tetrahedron, closest to
+    the HBM roofline: n^3 grid, 8 bands x 8 orbitals, 200 bins (bin mode), the
+    orbital weights stored in FP32 / FP16 / BF16. Per weight type: DOS time,
+    the algorithmic input bytes of one launch (eps + weights of every padded
+    point, read once) and their rate against the measured HBM copy bandwidth,
+    and the deviation from the FP32-weight DOS."""
+    import tbgen
+    mp = {}
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(mp.get("hbm_gbs", 6800.0))
+    out = {"workload": f"{n}^3 grid, 8 bands, 8 orbitals, {nbins} bins (bin mode), FP32 arithmetic",
+           "hbm_peak_gbs": hbm, "hbm_peak_source": "hbm_gbs of MEASURED_PEAKS.json" if mp else "fallback"}
+    edges = d32 = None
+    for wd in ("f32", "f16", "bf16"):
+        plan = T.Plan(n, n, n, 8, 8, nbins, mode="bin", weight_dtype=wd, device=local)
+        eps, w = plan.empty_inputs()
+        plan.eig(params, R, eps, w)
+        torch.cuda.synchronize()
+        if edges is None:
+            lo, hi = float(eps[..., :8].min()) - 0.1, float(eps[..., :8].max()) + 0.1
+            edges = torch.from_numpy(tbgen.bin_edges(lo, hi, nbins)).to(eps.device)
+        d = torch.empty((8, nbins), dtype=torch.float32, device=eps.device)
+        ms = time_dos(torch, plan, eps, w, edges, d, steps, warmup)
+        assert plan.status() == T.TETRA_OK
+        nbytes = (n + 1) ** 3 * 8 * (4 + 8 * (4 if wd == "f32" else 2))
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        if d32 is None:
+            d32 = d.clone()
+        out[wd] = {"dos_ms": ms, "algorithmic_input_bytes": nbytes, "input_gbs": gbs,
+                   "frac_of_hbm": gbs / hbm,
+                   "max_rel_dev_vs_f32_weights": float((d - d32).abs().max() / d32.abs().max())}
+        del eps, w, plan
+        torch.cuda.empty_cache()
+    return out
 
 
 def precision_variants(torch, T, n, nw, mode, params, R, omega, dos32, steps, warmup, local):
@@ -556,10 +596,16 @@ def main():
     dev = torch.device("cuda", local)
     T.build()
     if args.variant is not None:
-        fn = {"differentiation": differentiation_workload, "paper_shape": paper_shape_workload,
-              "lindhard": lindhard_workload}[args.variant]
+        if args.variant == "near_balance":
+            p_np, R_np = model_arrays(tbgen.tb_model(rank, n_orb=8))
+            r = near_balance_workload(torch, T, args.grid, torch.from_numpy(p_np).to(dev),
+                                      torch.from_numpy(R_np).to(dev), args.steps, args.warmup, local)
+        else:
+            fn = {"differentiation": differentiation_workload, "paper_shape": paper_shape_workload,
+                  "lindhard": lindhard_workload}[args.variant]
+            r = fn(torch, T, args.steps, args.warmup, local)
         if rank == 0:
-            print(json.dumps(fn(torch, T, args.steps, args.warmup, local)), flush=True)
+            print(json.dumps(r), flush=True)
         return
     n, nw = args.grid, args.n_omega
     model = tbgen.tb_model(rank, n_orb=8)
@@ -673,6 +719,7 @@ def main():
         if args.mode == "point" and args.weight_dtype == "f32":
             variants["integrated"] = integrated_workload(torch, T, n, eps, w, args.steps, args.warmup, local)
         variants["lindhard"] = lindhard_workload(torch, T, args.steps, args.warmup, local)
+        variants["near_balance"] = near_balance_workload(torch, T, n, params, R, args.steps, args.warmup, local)
     cb = None
     if not args.no_cpu_baseline:
         cb = cpu_baseline(n, nw, seed=0, stride=4)

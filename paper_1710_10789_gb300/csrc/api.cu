@@ -66,11 +66,11 @@ int pow2_floor(int v) {
 }
 
 // Default box of cubes for a band count: 4 x 4 x BZ with at most ~1536 work
-// items per box (a work item is a (tetrahedron pair, band) in point and
-// integrated mode with up to 8 orbitals, a (tetrahedron, band) otherwise), which keeps the per-item
+// items per box (a work item is a (tetrahedron pair, band) with up to 8
+// orbitals, a (tetrahedron, band) with more), which keeps the per-item
 // fixed-point cap of the int32 tile (2^30 / items) above typical values.
 void default_box(const tetra_desc_t &d, int box[3]) {
-    const bool pairs = (d.mode == TETRA_POINT || d.mode == TETRA_INTEGRATED) && tetra::norb_template(d.n_orb) <= 8;
+    const bool pairs = tetra::norb_template(d.n_orb) <= 8;
     const int per_cube = (pairs ? 3 : 6) * std::max(1, d.n_bands);
     box[0] = env_int("TETRA_BOX_X", 4);
     box[1] = env_int("TETRA_BOX_Y", 4);
@@ -93,10 +93,9 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     // TMA slots (128-byte multiples): two of a box's energies, one of its weights
     const size_t e_stage = (npts * P.eps_stride * 4 + 127) & ~size_t(127);
     const size_t w_stage = (npts * P.w_stride * P.wbytes + 127) & ~size_t(127);
-    // point and integrated mode with up to 8 orbitals: one item per
-    // face-sharing tetrahedron pair (3 per cube); otherwise one item per
-    // tetrahedron (6 per cube)
-    const bool pairs = (d.mode == TETRA_POINT || d.mode == TETRA_INTEGRATED) && tetra::norb_template(d.n_orb) <= 8;
+    // up to 8 orbitals: one item per face-sharing tetrahedron pair (3 per
+    // cube); more: one item per tetrahedron (6 per cube)
+    const bool pairs = tetra::norb_template(d.n_orb) <= 8;
     P.items_per_box = (pairs ? 3 : 6) * P.BX * P.BY * P.BZ * d.n_bands;
     if (P.items_per_box > 65535) return TETRA_EUNSUPPORTED;
     P.tile_stride = tetra::norb_template(d.n_orb) + 1;

@@ -66,7 +66,7 @@ constexpr uint32_t kSmemAlign = 1024;
 // sub-partition) can use 168 registers per thread, 16 warps 128.
 template <int MODE, int NORB>
 struct Cfg {
-    static constexpr bool pairs = (MODE == TETRA_POINT || MODE == TETRA_INTEGRATED) && NORB <= 8;
+    static constexpr bool pairs = NORB <= 8;
     static constexpr int threads = pairs ? 384 : 512;
     static constexpr int max_regs = pairs ? 168 : 128;
     static constexpr int units_per_cube = pairs ? 3 : 6;
@@ -889,6 +889,58 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                             if (s >= A.n_orb) continue;
                             if (stepa) deposit_one(sa[s] + dith, Gsc + (long)s * A.chunk_w + (hsa - w0), A.status);
                             if (stepb) deposit_one(sb[s] + dith, Gsc + (long)s * A.chunk_w + (hsb - w0), A.status);
+                        }
+                    }
+                    continue;
+                }
+                if constexpr (MODE == TETRA_BIN) {
+                    // Bin averages: each tetrahedron's weight step over the bin
+                    // divided by its width (zero below E1; above E4 the weights
+                    // are saturated and their steps vanish), bins walked in
+                    // order so each upper edge's weights serve the next bin.
+                    float qmax = bmax * 8.f * fq * max_iw * 1.01f;
+                    if (!(ea[3] > ea[0]) || !(eb[3] > eb[0])) qmax = 3.0e38f;
+                    const bool fast = qmax < (float)A.fast_cap;
+                    if (fast && hi >= lo) {
+                        const unsigned qbnd = (unsigned)qmax + 2u;
+                        for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
+                        atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
+                        atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
+                    }
+                    Tet TA, TB;
+                    tet_setup(TA, ea[0], ea[1], ea[2], ea[3], fq);
+                    tet_setup(TB, eb[0], eb[1], eb[2], eb[3], fq);
+                    float wpa[4], wpb[4];
+                    tet_weights(TA, om[lo - w0], wpa);
+                    tet_weights(TB, om[lo - w0], wpb);
+                    int *col = tile + (lo - w0) * TS;
+                    for (int i = lo; i <= hi; ++i, col += TS) {
+                        float wna[4], wnb[4], da[4], db[4];
+                        tet_weights(TA, om[i + 1 - w0], wna);
+                        tet_weights(TB, om[i + 1 - w0], wnb);
+                        const float sc = iw[i - w0];
+#pragma unroll
+                        for (int r4 = 0; r4 < 4; ++r4) {
+                            da[r4] = (wna[r4] - wpa[r4]) * sc;
+                            wpa[r4] = wna[r4];
+                            db[r4] = (wnb[r4] - wpb[r4]) * sc;
+                            wpb[r4] = wnb[r4];
+                        }
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            if (!fast && s >= A.n_orb) continue;
+                            float acc = fmaf(ba[0][s], da[0], dith);
+                            acc = fmaf(ba[1][s], da[1], acc);
+                            acc = fmaf(ba[2][s], da[2], acc);
+                            acc = fmaf(ba[3][s], da[3], acc);
+                            acc = fmaf(bb[0][s], db[0], acc);
+                            acc = fmaf(bb[1][s], db[1], acc);
+                            acc = fmaf(bb[2][s], db[2], acc);
+                            acc = fmaf(bb[3][s], db[3], acc);
+                            if (fast)
+                                atomicAdd(col + s, __float_as_int(acc + kMagic));
+                            else
+                                deposit_one(acc, Gc + (long)s * A.chunk_w + (i - w0), A.status);
                         }
                     }
                     continue;
