@@ -113,7 +113,7 @@ size_t tetra_workspace_bytes(tetra_plan_t plan);
  *                           (Eq. (2) with the step function as occupation;
  *                           not in the paper, which integrates the DOS only).
  *                           The whole energy grid must fit one shared-memory
- *                           tile (about 2000 energies for 8 orbitals; the plan
+ *                           tile (about 2400 energies for 8 orbitals; the plan
  *                           returns TETRA_EUNSUPPORTED otherwise).
  *            Normalised per spin and orbital: with unitary weights the bin
  *            DOS of each orbital integrates to 1, and n_s(E) rises from 0 to 1.
@@ -224,8 +224,8 @@ typedef struct {
 /* Plans a batch of n_models (1..TETRA_MAX_BATCH) descriptions (host array).
  * tune may be NULL. Returns TETRA_EINVAL if the descriptions differ in n_bands,
  * n_orb, mode or weight_dtype or one is invalid, TETRA_EUNSUPPORTED if the
- * largest n_omega does not fit one shared-memory tile (about 4100 energies, or
- * 3700 bins, for 8 orbitals and 8 bands in F32 with the default box). The plan
+ * largest n_omega does not fit one shared-memory tile (about 4300 energies, or
+ * 3900 bins, for 8 orbitals and 8 bands in F32 with the default box). The plan
  * owns only host memory. */
 tetra_status_t tetra_plan_batched(tetra_batch_plan_t *plan, const tetra_desc_t *descs, int n_models,
                                   const tetra_tune_t *tune, int device);

@@ -5,8 +5,9 @@
 //  * The cube grid [0,n1) x [0,n2) x [z0,z1) is cut into boxes of BX*BY*BZ
 //    cubes. A persistent CTA walks a sequence of boxes and, for each, has the
 //    box's (BX+1)(BY+1)(BZ+1) corner points of all bands (energies and orbital
-//    weights, tetra layout) copied into shared memory by two 4-D TMA loads,
-//    double buffered across boxes. One model: boxes blockIdx.x, blockIdx.x +
+//    weights, tetra layout) copied into shared memory by two 4-D TMA loads:
+//    the energies double buffered across boxes, the weights (read only by the
+//    walks) in one slot loaded behind the next box's window pass. One model: boxes blockIdx.x, blockIdx.x +
 //    gridDim.x, ... (blockIdx.y = energy chunk). A batch of models: each CTA
 //    claims the next (model, box) item from a global counter (models in
 //    order), so the work stays balanced whatever the models' costs; when the
@@ -17,11 +18,13 @@
 //    positions (Sec. II.C sorts E1 <= E2 <= E3 <= E4), reads the orbital
 //    weights in sorted order, and visits only the energies strictly inside
 //    (E1, E4) (bins overlapping it in bin mode); all others get zero weight.
-//  * Point mode (up to 8 orbitals): the item is a pair of tetrahedra sharing
+//  * Up to 8 orbitals (every mode): the item is a pair of tetrahedra sharing
 //    a face (Table I's six form three such pairs). Their windows overlap
 //    heavily, so one walk over the union of the two windows adds both
 //    tetrahedra's contributions at each energy before touching the shared
 //    tile: about half the shared-memory traffic of one tetrahedron each.
+//    (Integrated mode: each tetrahedron adds its weights below its own E4
+//    and puts its own saturation step.)
 //  * Items of a box are ranked by window length (counting sort), so the 32
 //    lanes of a warp walk windows of nearly equal length.
 //  * Each visited energy adds sum_l b_{l,s} dw_l to the CTA's tile for every
@@ -1151,7 +1154,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 }
             }
         }
-        __syncthreads();   // every thread is done reading both stages and adding to the tile
+        __syncthreads();   // every thread is done reading both slots and adding to the tile
         // refill: energies of work item k+2 into this energy stage, weights of k+1
         if (tid == 0) {
             fence_proxy_async_smem();
