@@ -67,6 +67,8 @@ def _load():
             lib.oracle_dos_range.restype = i
             lib.oracle_dos_bin_grad.argtypes = [i, i, i, i, i, d, d, i, d, d, d, d, d]
             lib.oracle_dos_bin_grad.restype = i
+            lib.oracle_table_i.argtypes = [ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_table_i.restype = None
             _lib = lib
     return _lib
 
@@ -80,6 +82,14 @@ def _c64(a) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- per tetrahedron
+def table_i() -> np.ndarray:
+    """The oracle's tetrahedron table (Table I): (6, 4) corner labels 1..8."""
+    lib = _load()
+    out = np.zeros(24, dtype=np.int32)
+    lib.oracle_table_i(out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return out.reshape(6, 4)
+
+
 def corner_weights(e_sorted, E: float, f: float):
     """(w[4], dw/dE[4]) of one tetrahedron with sorted corner energies."""
     lib = _load()

@@ -36,6 +36,14 @@
 static const int TABLE_I[6][4] = {
     {1, 2, 3, 6}, {2, 3, 4, 6}, {1, 3, 5, 6}, {3, 4, 6, 8}, {3, 5, 6, 7}, {3, 6, 7, 8}};
 
+/* The table above, row by row (24 labels), so tests can compare it with the
+ * printed Table I. */
+void oracle_table_i(int out[24]) {
+    int t, q;
+    for (t = 0; t < 6; ++t)
+        for (q = 0; q < 4; ++q) out[4 * t + q] = TABLE_I[t][q];
+}
+
 /*
  * Corner weights w_j(E) and their energy derivatives dw_j/dE for one
  * tetrahedron with sorted corner energies e[0] <= e[1] <= e[2] <= e[3]
