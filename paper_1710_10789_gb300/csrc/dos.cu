@@ -818,7 +818,9 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     int loa, hia, lob, hib;
                     item_window<MODE>(ea[0], ea[3], om, w0, wc, om0, inv_de, M.n_omega, loa, hia);
                     item_window<MODE>(eb[0], eb[3], om, w0, wc, om0, inv_de, M.n_omega, lob, hib);
-                    const int hsa = hia + 1, hsb = hib + 1;
+                    // the first energy with saturated weights: at or above E4 and
+                    // above E1 (a flat tetrahedron, E1 = E4, is empty at E = E1)
+                    const int hsa = max(hia + 1, loa), hsb = max(hib + 1, lob);
                     const bool stepa = hsa < w0 + wc, stepb = hsb < w0 + wc;
                     if (fast) {
                         const unsigned qbnd = (unsigned)qmax + 2u;

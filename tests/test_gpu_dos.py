@@ -32,7 +32,7 @@ def T():
 def run_gpu(T, eps, w, n, omega, mode="point", wdtype="f32", z_range=None, n_omega=None):
     n1, n2, n3 = n
     nb, no = eps.shape[1], w.shape[2]
-    nw = len(omega) if mode == "point" else len(omega) - 1
+    nw = len(omega) - 1 if mode == "bin" else len(omega)
     plan = T.Plan(n1, n2, n3, nb, no, nw, mode=mode, weight_dtype=wdtype, z_range=z_range)
     L = plan.layout
     npw = {"f32": np.float32, "f16": np.float16, "bf16": np.float32}[wdtype]
@@ -136,6 +136,34 @@ def test_flat_band_point_and_bin(T):
     r = oracle.dos(eps, w, *n, edges.astype(np.float64), mode="bin")
     assert_parity(g, r)
     np.testing.assert_allclose((g[0] * np.diff(edges.astype(np.float64))).sum(), 1.0, rtol=1e-6)
+
+
+def test_partly_flat_bands_every_mode(T):
+    """Bands flat over part of the grid: face-sharing pairs then hold one flat
+    and one dispersive tetrahedron (the bin-mode pair takes the exact 64-bit
+    path, the integrated pair puts two steps), next to fully flat and fully
+    dispersive pairs. Point, bin and integrated mode against the oracle."""
+    n = (8, 7, 6)
+    x, y, z = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    x, y, z = (a.transpose(2, 1, 0).ravel() for a in (x, y, z))   # k = x + n1 (y + n2 z)
+    c = np.cos(2 * np.pi * x / n[0]) + 0.5 * np.cos(2 * np.pi * y / n[1]) + 0.3 * np.cos(2 * np.pi * z / n[2])
+    # exactly flat where c <= 0.2 (values within 1e-3 of the level snapped onto
+    # it: a window of width ~1e-17 with a grid energy inside would make the
+    # point DOS exceed the fixed-point range, which the kernel reports as
+    # TETRA_ERANGE instead of computing)
+    flat = np.where(c - 0.2 > 1e-3, c - 0.2, 0.0)
+    eps = np.stack([flat, np.full(c.shape, 0.7), c], axis=1).astype(np.float32)
+    w = np.random.default_rng(5).uniform(0.1, 1.0, (eps.shape[0], 3, 2)).astype(np.float32)
+    omega = tbgen.uniform_grid(-1.9, 2.0, 79)
+    g, *_ = run_gpu(T, eps, w, n, omega)
+    assert_parity(g, oracle.dos(eps, w, *n, omega.astype(np.float64)))
+    edges = tbgen.bin_edges(-1.95, 2.05, 40)
+    g, *_ = run_gpu(T, eps, w, n, edges, mode="bin")
+    r = oracle.dos(eps, w, *n, edges.astype(np.float64), mode="bin")
+    assert_parity(g, r)
+    g, *_ = run_gpu(T, eps, w, n, omega, mode="integrated")
+    r = oracle.dos(eps, w, *n, omega.astype(np.float64), mode="integrated")
+    assert_parity(g, r)
 
 
 def test_flat_band_level_on_a_bin_edge(T):
