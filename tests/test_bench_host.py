@@ -37,3 +37,16 @@ def test_reference_arm_line_matches_the_gpu_arm_config():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_defaults_and_variant_flag(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert (a.gpus, a.impl, a.grid, a.n_omega, a.mode, a.weight_dtype, a.variant) == \
+        (1, "ours", 256, 4000, "point", "f32", None)
+    assert a.warmup >= 3
+    c = bench.config_of(a, 1)
+    assert c["workload"] == "tb8_256cube_4000w_point_f32" and c["tetrahedra"] == 6 * 256 ** 3
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--variant", "near_balance", "--steps", "2"])
+    a = bench.parse()
+    assert a.variant == "near_balance" and a.steps == 2
