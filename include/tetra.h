@@ -296,7 +296,11 @@ tetra_status_t tetra_pair_bands(tetra_plan_t plan, const float *eps, const int q
                                 tetra_plan_t pair_plan, float *eps_pairs, float *w_pairs, cudaStream_t stream);
 
 /* Device-side status recorded in a workspace by the last call that used it
- * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. */
+ * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. The
+ * fixed-point accumulation of tetra_dos raises TETRA_ERANGE (and leaves that
+ * contribution out) when one contribution exceeds the 64-bit range: in point
+ * mode a nearly flat tetrahedron (energy spread below ~1e-12 eV for typical
+ * grids) with a grid energy inside its window, whose DOS there is ~3/E41. */
 tetra_status_t tetra_workspace_status(const void *ws, cudaStream_t stream);
 
 /* Human-readable name of a status. */
