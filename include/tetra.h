@@ -134,19 +134,30 @@ tetra_status_t tetra_dos(tetra_plan_t plan, const float *eps, const void *w,
  *   GPU that loads the library until the process exits). The call allocates
  *   nothing. If the plan's per-CTA partial sums do not fit, fewer persistent
  *   CTAs are used (same result, bit for bit); if they do not fit even with one
- *   CTA (n_orb * n_omega * 8 bytes, twice that in TETRA_INTEGRATED mode, plus
- *   256 bytes, above 32 MiB), returns TETRA_ENOMEM.
+ *   CTA, returns TETRA_ENOMEM. With one CTA the scratch holds
+ *     256 + m * 8 * n_orb * n_chunks * ceil(n_omega / n_chunks)  bytes,
+ *   m = 2 in TETRA_INTEGRATED mode and 1 otherwise, where n_chunks is the
+ *   number of shared-memory energy tiles of the plan (1 up to about 4300
+ *   energies for 8 orbitals and 8 bands in F32).
  *   Set-up: the first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   before any stream capture. The address is kept with the device's context;
+ *   after a device reset the next call looks it up again.
  *   Sharing: every call on a device uses the same array, and the call clears
  *   what it needs before use. Calls whose kernels overlap on the GPU (different
  *   streams, or host threads) race on the array and give wrong results;
- *   serialise them. Device-side status words of this variant are not reported
- *   (use tetra_dos with a workspace and tetra_workspace_status to diagnose).
+ *   serialise them. The array keeps the last call's contents, including its
+ *   device-side status words: read them with tetra_noalloc_status().
  * Arguments and results are those of tetra_dos. */
 tetra_status_t tetra_dos_noalloc(tetra_plan_t plan, const float *eps, const void *w,
                                  const float *omega, float *dos, cudaStream_t stream);
+
+/* Device-side status of the last tetra_dos_noalloc call on `device`, read
+ * from the front of its static scratch array (synchronises `stream`, which
+ * must be a stream of `device` or 0). TETRA_OK, TETRA_ETIMEOUT or
+ * TETRA_ERANGE, as tetra_workspace_status() gives for tetra_dos; TETRA_OK if
+ * no tetra_dos_noalloc call has run on the device yet. Not in the paper. */
+tetra_status_t tetra_noalloc_status(int device, cudaStream_t stream);
 
 /* Adjoint of tetra_dos in TETRA_BIN mode (not in the paper; the derivative of
  * its bin-averaged DOS). Given grad_dos = dL/d dos [n_orb][n_omega], writes
@@ -216,8 +227,9 @@ typedef struct tetra_batch_plan_s *tetra_batch_plan_t;
 /* Launch-shape choices (e.g. from an autotuner); zero fields take the default. */
 typedef struct {
     int box_x, box_y, box_z; /* cubes per box side (rounded down to powers of two
-                                and clipped to the smallest grid); default 4,4,2
-                                for 8 bands                                        */
+                                and clipped to the smallest grid); default 4,4,4
+                                for 8 bands and up to 8 orbitals, 4,4,2 for 8
+                                bands and 9 to 16 orbitals                         */
     int ctas_per_sm;         /* persistent CTAs per SM, default 1                  */
 } tetra_tune_t;
 

@@ -7,7 +7,8 @@
  * cpu_baseline leg of bench.py may load or run it. It shares no code with the
  * CUDA library and must never be called from the product path.
  *
- * Conventions (each is a reading of the paper, recorded in the design doc):
+ * Conventions (each is a reading of the paper where the text is silent or
+ * ambiguous):
  *  - k-grid: periodic, Gamma-centred, n1 x n2 x n3 points, flat index
  *    k = x + n1*(y + n2*z). Every point is the origin corner of one
  *    elemental cube, so there are n1*n2*n3 cubes and 6*n1*n2*n3 tetrahedra.

@@ -23,7 +23,8 @@ __all__ = [
     "TetraError", "TetraDesc", "TetraLayout", "TetraModel", "build", "lib", "lib_path",
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
-    "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc", "Plan",
+    "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc",
+    "tetra_noalloc_status", "Plan",
     "EXPORTED_SYMBOLS", "TetraTune", "tetra_plan_batched", "tetra_batch_plan_destroy",
     "tetra_batch_layout", "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
     "BatchPlan", "TETRA_MAX_BATCH", "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
@@ -40,7 +41,7 @@ EXPORTED_SYMBOLS = (
     "tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_workspace_bytes", "tetra_dos",
     "tetra_dos_backward", "tetra_eig", "tetra_eig_backward", "tetra_eig_workspace_bytes",
     "tetra_workspace_status", "tetra_strerror", "tetra_version", "tetra_dos_noalloc",
-    "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
+    "tetra_noalloc_status", "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
     "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
     "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
 )
@@ -107,6 +108,7 @@ def lib():
             L.tetra_workspace_bytes.restype = sz
             L.tetra_dos.argtypes = [vp, vp, vp, vp, vp, vp, sz, vp]
             L.tetra_dos_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
+            L.tetra_noalloc_status.argtypes = [i, vp]
             L.tetra_dos_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
             L.tetra_eig.argtypes = [vp, ctypes.POINTER(TetraModel), vp, vp, vp]
             L.tetra_eig_backward.argtypes = [vp, ctypes.POINTER(TetraModel), vp, vp, vp, vp, sz, vp]
@@ -132,7 +134,7 @@ def lib():
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
             for name in ("tetra_plan", "tetra_plan_destroy", "tetra_layout", "tetra_dos",
-                         "tetra_dos_noalloc",
+                         "tetra_dos_noalloc", "tetra_noalloc_status",
                          "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
                          "tetra_workspace_status", "tetra_plan_batched",
                          "tetra_batch_plan_destroy", "tetra_batch_layout", "tetra_batch_info",
@@ -188,6 +190,11 @@ def tetra_pair_bands(plan, eps, q, kT, mu, pair_plan, eps_pairs, w_pairs, stream
 def tetra_dos_noalloc(plan, eps, w, omega, dos, stream) -> int:
     """tetra_dos with the library's fixed scratch instead of a workspace (see tetra.h)."""
     return lib().tetra_dos_noalloc(plan, eps, w, omega, dos, stream)
+
+
+def tetra_noalloc_status(device, stream) -> int:
+    """Device-side status of the last tetra_dos_noalloc call on `device`."""
+    return lib().tetra_noalloc_status(int(device), stream)
 
 
 def tetra_dos_backward(plan, eps, w, omega, grad_dos, grad_eps, grad_w, ws, ws_bytes, stream) -> int:

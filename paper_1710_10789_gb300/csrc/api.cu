@@ -229,7 +229,8 @@ tetra_status_t tetra_dos(tetra_plan_t plan, const float *eps, const void *w, con
     if (!plan || !eps || !w || !omega || !dos || !ws) return TETRA_EINVAL;
     if (!tetra::aligned16(eps) || !tetra::aligned16(w) || !tetra::aligned16(ws)) return TETRA_EINVAL;
     if (ws_bytes < tetra::dos_forward_workspace(*plan)) return TETRA_ENOMEM;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::launch_dos_forward(*plan, eps, w, omega, dos, ws, ws_bytes, stream);
 }
 
@@ -240,7 +241,8 @@ tetra_status_t tetra_dos_backward(tetra_plan_t plan, const float *eps, const voi
     if (plan->d.mode != TETRA_BIN) return TETRA_EUNSUPPORTED;
     if (!tetra::aligned16(eps) || !tetra::aligned16(w) || !tetra::aligned16(ws)) return TETRA_EINVAL;
     if (ws_bytes < tetra::dos_backward_workspace(*plan)) return TETRA_ENOMEM;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::launch_dos_backward(*plan, eps, w, omega, grad_dos, grad_eps, grad_w, ws,
                                       ws_bytes, stream);
 }
@@ -249,7 +251,8 @@ tetra_status_t tetra_eig(tetra_plan_t plan, const tetra_model_t *model, float *e
                          cudaStream_t stream) {
     if (!plan || !model || !eps || !w) return TETRA_EINVAL;
     if (!tetra::aligned16(eps) || !tetra::aligned16(w)) return TETRA_EINVAL;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::launch_eig(*plan, model, eps, w, stream);
 }
 
@@ -264,7 +267,8 @@ tetra_status_t tetra_eig_backward(tetra_plan_t plan, const tetra_model_t *model,
     if (!plan || !model || !grad_eps || !grad_w || !grad_params || !ws) return TETRA_EINVAL;
     if (!tetra::aligned16(ws)) return TETRA_EINVAL;
     if (ws_bytes < tetra::eig_backward_workspace(*plan, model->n_R)) return TETRA_ENOMEM;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::launch_eig_backward(*plan, model, grad_eps, grad_w, grad_params, ws, ws_bytes,
                                       stream);
 }
@@ -370,7 +374,8 @@ tetra_status_t tetra_dos_batched(tetra_batch_plan_t plan, const float *const *ep
         if (!tetra::aligned16(eps[m]) || !tetra::aligned16(w[m])) return TETRA_EINVAL;
     }
     if (ws_bytes < tetra::dos_batched_workspace(*plan)) return TETRA_ENOMEM;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::launch_dos_batched(*plan, eps, w, omega, dos, ws, ws_bytes, stream);
 }
 

@@ -155,6 +155,7 @@ extern "C" tetra_status_t tetra_fermi_level(tetra_plan_t plan, const float *eps,
     if ((reinterpret_cast<uintptr_t>(eps) & 15u) || (reinterpret_cast<uintptr_t>(w) & 15u) ||
         (reinterpret_cast<uintptr_t>(ws) & 15u))
         return TETRA_EINVAL;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::fermi_level(*plan, eps, w, n_electrons, ef, ws, ws_bytes, stream);
 }

@@ -10,6 +10,8 @@
 // argument. The caller still passes inputs and outputs.
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "tetra_internal.cuh"
 
 namespace tetra {
@@ -24,18 +26,47 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
+// Per device: the array's device address and the context it was looked up in.
+// A device reset destroys the context (and the address with it); the next
+// call sees a different current context and looks the address up again.
 void *g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on `device` (which must be current).
+PFN_cuCtxGetCurrent_v4000 ctx_fn() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    });
+    return fn;
+}
+
+// Device address of the scratch array on `device`, which the caller has made
+// current with cudaSetDevice (so its primary context is current).
 // In host code the array's name only stands for the device symbol, so the
-// address is fetched once per device with cudaGetSymbolAddress.
-tetra_status_t scratch_address(int device, void **ptr) {
+// address is fetched with cudaGetSymbolAddress, once per device and context.
+// `lookup` false: return the cached address only (nullptr if none).
+tetra_status_t scratch_address(int device, void **ptr, bool lookup) {
     if (device < 0 || device >= kMaxDevices) return TETRA_EUNSUPPORTED;
+    CUcontext ctx = nullptr;
+    auto fn = ctx_fn();
+    if (!fn || fn(&ctx) != CUDA_SUCCESS || !ctx) return TETRA_ECUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[device]) {
+    if (!g_scratch_ptr[device] || g_scratch_ctx[device] != ctx) {
+        g_scratch_ptr[device] = nullptr;
+        if (!lookup) {
+            *ptr = nullptr;
+            return TETRA_OK;
+        }
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TETRA_ECUDA;
         g_scratch_ptr[device] = p;
+        g_scratch_ctx[device] = ctx;
     }
     *ptr = g_scratch_ptr[device];
     return TETRA_OK;
@@ -56,10 +87,21 @@ extern "C" tetra_status_t tetra_dos_noalloc(tetra_plan_t plan, const float *eps,
     tetra::Plan q = *plan;
     while (q.grid_x > 1 && tetra::dos_forward_workspace(q) > tetra::kNoAllocScratchBytes) --q.grid_x;
     if (tetra::dos_forward_workspace(q) > tetra::kNoAllocScratchBytes) return TETRA_ENOMEM;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     void *scratch = nullptr;
-    const tetra_status_t st = tetra::scratch_address(plan->device, &scratch);
+    const tetra_status_t st = tetra::scratch_address(plan->device, &scratch, true);
     if (st != TETRA_OK) return st;
     return tetra::launch_dos_forward(q, eps, w, omega, dos, scratch, tetra::kNoAllocScratchBytes,
                                      stream);
+}
+
+extern "C" tetra_status_t tetra_noalloc_status(int device, cudaStream_t stream) {
+    const tetra::DeviceGuard dg(device);
+    if (!dg.ok()) return TETRA_ECUDA;
+    void *scratch = nullptr;
+    const tetra_status_t st = tetra::scratch_address(device, &scratch, false);
+    if (st != TETRA_OK) return st;
+    if (!scratch) return TETRA_OK;   // no tetra_dos_noalloc call on this device and context yet
+    return tetra_workspace_status(scratch, stream);
 }

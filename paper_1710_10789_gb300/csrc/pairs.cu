@@ -98,6 +98,7 @@ extern "C" tetra_status_t tetra_pair_bands(tetra_plan_t plan, const float *eps, 
     if ((reinterpret_cast<uintptr_t>(eps) & 15u) || (reinterpret_cast<uintptr_t>(eps_pairs) & 15u) ||
         (reinterpret_cast<uintptr_t>(w_pairs) & 15u))
         return TETRA_EINVAL;
-    if (cudaSetDevice(plan->device) != cudaSuccess) return TETRA_ECUDA;
+    const tetra::DeviceGuard dg(plan->device);
+    if (!dg.ok()) return TETRA_ECUDA;
     return tetra::launch_pair_bands(*plan, eps, q, kT, mu, *pair_plan, eps_pairs, w_pairs, stream);
 }

@@ -177,6 +177,31 @@ __device__ __forceinline__ void load_weights(const WT *src, int n_orb, float (&b
 }
 
 // ---------------------------------------------------------------- host helpers
+// Makes `device` current for the lifetime of the guard and restores the
+// caller's current device afterwards, so an entry point leaves the calling
+// thread's device as it found it.
+class DeviceGuard {
+  public:
+    // cudaSetDevice is called even when `device` is already current: it also
+    // makes the device's primary context current on the calling thread.
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) return;
+        ok_ = cudaSetDevice(device) == cudaSuccess;
+        switched_ = ok_ && prev_ != device;
+    }
+    ~DeviceGuard() {
+        if (switched_) cudaSetDevice(prev_);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+    bool ok() const { return ok_; }
+
+  private:
+    int prev_ = 0;
+    bool ok_ = false;
+    bool switched_ = false;
+};
+
 tetra_status_t encode_point_map(CUtensorMap *map, const void *base, CUtensorMapDataType dtype,
                                 int elem_bytes, int stride_elems, int nx, int ny, int nz,
                                 int box_x, int box_y, int box_z);

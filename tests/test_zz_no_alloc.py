@@ -11,6 +11,7 @@ run that stops at the first failure has run every other test before it.
 import numpy as np
 import pytest
 
+import tbgen
 from helpers import energy_window, tb_problem, to_layout
 
 torch = pytest.importorskip("torch")
@@ -50,6 +51,44 @@ def test_noalloc_matches_workspace_entry_point():
         g = out.cpu().numpy().astype(np.float64)
         err = np.max(np.abs(g - r))
         assert err <= TOL * np.max(np.abs(r)), (call, err)
+        assert T.tetra_noalloc_status(torch.cuda.current_device(), stream) == T.TETRA_OK
+
+
+SCRATCH = 32 << 20
+
+
+@pytest.mark.parametrize("mode,n_omega", [("point", 4000), ("bin", 3800), ("integrated", 2000)])
+def test_noalloc_with_fewer_ctas_is_bitwise_equal(mode, n_omega):
+    """Problems whose per-CTA partial sums exceed the 32 MiB scratch with one
+    CTA per SM run on fewer CTAs; the exact integer accumulation makes the
+    result bit-identical to tetra_dos with a full workspace."""
+    import paper_1710_10789_gb300 as T
+
+    T.build()
+    n = 24   # 6^3 = 216 boxes of 4^3 cubes: one CTA per SM with the default plan
+    eps, w = tbgen.synthetic_bands(3, n, n, n, 8, 8)
+    lo, hi = float(eps.min()) - 0.1, float(eps.max()) + 0.1
+    omega = tbgen.bin_edges(lo, hi, n_omega) if mode == "bin" else tbgen.uniform_grid(lo, hi, n_omega)
+    plan = T.Plan(n, n, n, 8, 8, n_omega, mode=mode)
+    L = plan.layout
+    E, W = to_layout(eps.astype(np.float32), w.astype(np.float32), n, n, n, L.eps_stride, L.w_stride)
+    dev = torch.device("cuda")
+    Et, Wt, om = (torch.from_numpy(a).to(dev) for a in (E, W, omega))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    parts = 256 + (2 if mode == "integrated" else 1) * 8 * 8 * min(216, sms) * n_omega
+    assert parts > SCRATCH, "the case must not fit the scratch with the default CTA count"
+    ref = plan.dos(Et, Wt, om)
+    torch.cuda.synchronize()
+    assert plan.status() == T.TETRA_OK
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        out = torch.full_like(ref, float("nan"))
+        st = T.tetra_dos_noalloc(plan.handle, Et.data_ptr(), Wt.data_ptr(), om.data_ptr(), out.data_ptr(),
+                                 stream)
+        assert st == T.TETRA_OK, T.tetra_strerror(st)
+        torch.cuda.synchronize()
+        assert T.tetra_noalloc_status(torch.cuda.current_device(), stream) == T.TETRA_OK
+        assert torch.equal(out, ref), (mode, call)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
