@@ -15,6 +15,11 @@ Pieces and the passages they follow (arXiv:1710.10789):
     definition of the corner weights (C code).
   * ``eig_backward``: first-order perturbation theory of the Hermitian
     eigenproblem, chained to the hopping parameters of Eq. (1).
+  * ``pair_bands`` / ``spectral_t0``: the spectral part of the bare
+    susceptibility, the extension the paper names (abstract, Conclusions):
+    with Fermi-Dirac occupations interpolated linearly (pair bands fed to
+    ``dos``), and at T = 0 with step occupations clipped exactly inside each
+    tetrahedron (C code).
 
 Every numerical convention (grid, corner labels, region boundaries, the
 corrected dw3/dE term) is listed in the header of ``tetra_oracle.c``.
@@ -69,6 +74,11 @@ def _load():
             lib.oracle_dos_bin_grad.restype = i
             lib.oracle_table_i.argtypes = [ctypes.POINTER(ctypes.c_int)]
             lib.oracle_table_i.restype = None
+            lib.oracle_t0_tetra.argtypes = [d, d, i, i, d, d, d]
+            lib.oracle_t0_tetra.restype = None
+            lib.oracle_t0_spectral.argtypes = [i, i, i, i, d, d, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                               i, i, d, d, i, i, d]
+            lib.oracle_t0_spectral.restype = i
             _lib = lib
     return _lib
 
@@ -320,3 +330,51 @@ def pair_bands(eps, n1, n2, n3, q, kT, mu):
     delta = (e_kq[:, None, :] - e_k[:, :, None]).reshape(nk, nb * nb)
     weight = (f_k[:, :, None] - f_kq[:, None, :]).reshape(nk, nb * nb, 1)
     return delta, weight
+
+
+# ---------------------------------------------------------------- spectral function at T = 0
+def _edges_pair(energies, mode, edges_hi):
+    if mode == "point":
+        ea = _c64(energies)
+        return ea, ea, 0
+    if edges_hi is None:
+        e = _c64(energies)
+        return np.ascontiguousarray(e[:-1]), np.ascontiguousarray(e[1:]), 1
+    return _c64(energies), _c64(edges_hi), 1
+
+
+def spectral_t0_tetra(a, c, energies, mode="point", edges_hi=None) -> np.ndarray:
+    """One tetrahedron's T = 0 spectral contribution in units of V_T/V_G:
+    a[4] = e_n - mu and c[4] = e_m(k+q) - mu at its corners; the transition
+    energy c - a over {a < 0, c > 0} counts +1, over {a > 0, c < 0} -1
+    (point density at ``energies``, or bin averages as in ``dos``)."""
+    lib = _load()
+    ea, eb, m = _edges_pair(energies, mode, edges_hi)
+    out = np.zeros(ea.shape[0])
+    lib.oracle_t0_tetra(_p(_c64(a)), _p(_c64(c)), m, ea.shape[0], _p(ea), _p(eb), _p(out))
+    return out
+
+
+def spectral_t0(eps, n1, n2, n3, q, mu, energies, mode="point", edges_hi=None, eps_kq=None,
+                z_range=None) -> np.ndarray:
+    """T = 0 spectral function of the bare susceptibility,
+    S(q, w) = sum_{n,m} (1/V_G) int [Theta(mu - e_n(k)) - Theta(mu - e_m(k+q))]
+              delta(w - e_m(k+q) + e_n(k)) dk,   Im chi0(q, w + i0) = -pi S,
+    with every band linear inside each tetrahedron and the step occupations
+    clipped exactly (C code, ``oracle_t0_spectral``). eps (nk, nb) natural
+    layout; eps_kq, if given, holds the bands at k + q on the same flat index
+    (otherwise eps shifted by the integer grid vector q). Returns (npts,)."""
+    lib = _load()
+    eps = _c64(eps)
+    nk, nb = eps.shape
+    assert nk == n1 * n2 * n3
+    epq = None if eps_kq is None else _c64(eps_kq)
+    ea, eb, m = _edges_pair(energies, mode, edges_hi)
+    out = np.zeros(ea.shape[0])
+    qa = (ctypes.c_int * 3)(*[int(v) for v in q])
+    z0, z1 = (0, n3) if z_range is None else z_range
+    rc = lib.oracle_t0_spectral(n1, n2, n3, nb, _p(eps), _p(epq) if epq is not None else None, qa,
+                                float(mu), m, ea.shape[0], _p(ea), _p(eb), int(z0), int(z1), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_t0_spectral failed ({rc})")
+    return out

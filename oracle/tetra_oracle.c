@@ -377,3 +377,235 @@ int oracle_dos_bin_grad(int n1, int n2, int n3, int nb, int norb, const double *
                 }
     return 0;
 }
+
+/* ---- bare susceptibility at T = 0: double-band tetrahedron clipping ------
+ *
+ * The spectral part of the bare (Lindhard) susceptibility with step
+ * occupations (T = 0), the extension to susceptibilities the paper names as
+ * its method's next use (abstract, Conclusions):
+ *   S(q, w) = sum_{n,m} (1/V_G) int dk [Theta(mu - e_n(k)) - Theta(mu - e_m(k+q))]
+ *                                  delta(w - (e_m(k+q) - e_n(k))),
+ * Im chi0(q, w + i0) = -pi S(q, w). With the method's linear interpolation
+ * inside every tetrahedron, a = e_n - mu, c = e_m(k+q) - mu and the transition
+ * energy D = c - a are linear there. The occupation difference is +1 on
+ * {a < 0, c > 0}, -1 on {a > 0, c < 0} and 0 elsewhere, so each tetrahedron
+ * contributes the distribution of D over two convex regions, each the
+ * tetrahedron clipped by two planes. The regions are cut into
+ * sub-tetrahedra; over a sub-tetrahedron of volume fraction nu, D is linear
+ * and its distribution is nu * g(w) with g the normalised single-tetrahedron
+ * density of a linear function (the total DOS of Sec. II.C's weights divided
+ * by V_T / V_G).
+ */
+
+/* A point of the parent tetrahedron: barycentric coordinates and the two
+ * linear fields. */
+typedef struct {
+    double l[4];
+    double a, c;
+} t0_point;
+
+static void t0_lerp(const t0_point *u, const t0_point *v, double t, t0_point *out) {
+    int i;
+    for (i = 0; i < 4; ++i) out->l[i] = u->l[i] + t * (v->l[i] - u->l[i]);
+    out->a = u->a + t * (v->a - u->a);
+    out->c = u->c + t * (v->c - u->c);
+}
+
+/* Field to clip by: field 0 -> s = a, field 1 -> s = -a, 2 -> c, 3 -> -c.
+ * The kept side is s < 0. */
+static double t0_field(const t0_point *p, int which) {
+    switch (which) {
+        case 0: return p->a;
+        case 1: return -p->a;
+        case 2: return p->c;
+        default: return -p->c;
+    }
+}
+
+/* Clips tetrahedron T (4 points) to {s < 0}; writes up to 3 tetrahedra that
+ * tile the kept part into out[], returns their number. */
+static int t0_clip(const t0_point T[4], int which, t0_point out[3][4]) {
+    int in[4], outv[4], ni = 0, no = 0, q;
+    double s[4];
+    for (q = 0; q < 4; ++q) {
+        s[q] = t0_field(&T[q], which);
+        if (s[q] < 0.0) in[ni++] = q;
+        else outv[no++] = q;
+    }
+    if (ni == 0) return 0;
+    if (ni == 4) {
+        for (q = 0; q < 4; ++q) out[0][q] = T[q];
+        return 1;
+    }
+#define T0_CUT(u, v, dst) t0_lerp(&T[u], &T[v], s[u] / (s[u] - s[v]), &(dst))
+    if (ni == 1) { /* corner tetrahedron at the one kept vertex */
+        const int i = in[0];
+        out[0][0] = T[i];
+        T0_CUT(i, outv[0], out[0][1]);
+        T0_CUT(i, outv[1], out[0][2]);
+        T0_CUT(i, outv[2], out[0][3]);
+        return 1;
+    }
+    if (ni == 3) { /* prism: kept face I1 I2 I3, cut face P1 P2 P3, Pj on edge (o, Ij) */
+        t0_point P[3];
+        const int o = outv[0];
+        for (q = 0; q < 3; ++q) T0_CUT(in[q], o, P[q]);
+        out[0][0] = T[in[0]]; out[0][1] = T[in[1]]; out[0][2] = T[in[2]]; out[0][3] = P[0];
+        out[1][0] = T[in[1]]; out[1][1] = T[in[2]]; out[1][2] = P[0]; out[1][3] = P[1];
+        out[2][0] = T[in[2]]; out[2][1] = P[0]; out[2][2] = P[1]; out[2][3] = P[2];
+        return 3;
+    }
+    { /* wedge: triangles (I1, P11, P12) and (I2, P21, P22), Pij on edge (Ii, Oj) */
+        t0_point P11, P12, P21, P22;
+        const int i1 = in[0], i2 = in[1], o1 = outv[0], o2 = outv[1];
+        T0_CUT(i1, o1, P11);
+        T0_CUT(i1, o2, P12);
+        T0_CUT(i2, o1, P21);
+        T0_CUT(i2, o2, P22);
+        out[0][0] = T[i1]; out[0][1] = P11; out[0][2] = P12; out[0][3] = T[i2];
+        out[1][0] = P11; out[1][1] = P12; out[1][2] = T[i2]; out[1][3] = P21;
+        out[2][0] = P12; out[2][1] = T[i2]; out[2][2] = P21; out[2][3] = P22;
+        return 3;
+    }
+#undef T0_CUT
+}
+
+/* Volume of a sub-tetrahedron as a fraction of its parent (barycentric). */
+static double t0_volume(const t0_point P[4]) {
+    double u[3][3];
+    int i, j;
+    for (i = 0; i < 3; ++i)
+        for (j = 0; j < 3; ++j) u[i][j] = P[i].l[j] - P[3].l[j];
+    return fabs(u[0][0] * (u[1][1] * u[2][2] - u[1][2] * u[2][1]) -
+                u[0][1] * (u[1][0] * u[2][2] - u[1][2] * u[2][0]) +
+                u[0][2] * (u[1][0] * u[2][1] - u[1][1] * u[2][0]));
+}
+
+/* Normalised density g(w) and cumulative G(w) of a linear function with the
+ * given values at the corners of a tetrahedron (uniform measure). */
+static void t0_density(const double d_in[4], double w, double *g, double *G) {
+    double d[4];
+    int i, j;
+    for (i = 0; i < 4; ++i) d[i] = d_in[i];
+    for (i = 1; i < 4; ++i) { /* insertion sort */
+        const double v = d[i];
+        j = i - 1;
+        while (j >= 0 && d[j] > v) { d[j + 1] = d[j]; --j; }
+        d[j + 1] = v;
+    }
+    if (w <= d[0]) { *g = 0.0; *G = 0.0; return; }
+    if (w >= d[3]) { *g = 0.0; *G = 1.0; return; }
+    {
+        const double d21 = d[1] - d[0], d31 = d[2] - d[0], d41 = d[3] - d[0];
+        const double d32 = d[2] - d[1], d42 = d[3] - d[1], d43 = d[3] - d[2];
+        if (w <= d[1]) {
+            const double x = w - d[0];
+            *g = 3.0 * x * x / (d21 * d31 * d41);
+            *G = x * x * x / (d21 * d31 * d41);
+        } else if (w <= d[2]) {
+            const double x = w - d[1];
+            *g = 3.0 / (d31 * d41) * (d21 + 2.0 * x - (d31 + d42) * x * x / (d32 * d42));
+            *G = (d21 * d21 + 3.0 * d21 * x + 3.0 * x * x - (d31 + d42) * x * x * x / (d32 * d42)) /
+                 (d31 * d41);
+        } else {
+            const double y = d[3] - w;
+            *g = 3.0 * y * y / (d41 * d42 * d43);
+            *G = 1.0 - y * y * y / (d41 * d42 * d43);
+        }
+    }
+}
+
+/*
+ * Contribution of one tetrahedron (vertex values a[4] = e_n - mu,
+ * c[4] = e_m(k+q) - mu) to the normalised spectral function, in units of
+ * V_T / V_G: mode 0 (point) sum_regions sign * nu * g(ea[i]); mode 1 (bin)
+ * sum_regions sign * nu * [G(eb[i]) - G(ea[i])] / (eb[i] - ea[i]). Adds to
+ * out[i], i < npts.
+ */
+void oracle_t0_tetra(const double a[4], const double c[4], int mode, int npts, const double *ea,
+                     const double *eb, double *out) {
+    t0_point T[4];
+    int q, r;
+    for (q = 0; q < 4; ++q) {
+        int j;
+        for (j = 0; j < 4; ++j) T[q].l[j] = (j == q) ? 1.0 : 0.0;
+        T[q].a = a[q];
+        T[q].c = c[q];
+    }
+    for (r = 0; r < 2; ++r) {
+        /* r = 0: {a < 0, c > 0}, sign +1; r = 1: {a > 0, c < 0}, sign -1 */
+        const double sign = r == 0 ? 1.0 : -1.0;
+        t0_point A[3][4];
+        const int na = t0_clip(T, r == 0 ? 0 : 1, A);
+        int ia;
+        for (ia = 0; ia < na; ++ia) {
+            t0_point B[3][4];
+            const int nbb = t0_clip(A[ia], r == 0 ? 3 : 2, B);
+            int ib;
+            for (ib = 0; ib < nbb; ++ib) {
+                const double nu = t0_volume(B[ib]);
+                double d[4];
+                int i;
+                if (nu <= 0.0) continue;
+                for (q = 0; q < 4; ++q) d[q] = B[ib][q].c - B[ib][q].a;
+                for (i = 0; i < npts; ++i) {
+                    double g, G, gb, Gb;
+                    t0_density(d, ea[i], &g, &G);
+                    if (mode == 0) {
+                        out[i] += sign * nu * g;
+                    } else {
+                        t0_density(d, eb[i], &gb, &Gb);
+                        out[i] += sign * nu * (Gb - G) / (eb[i] - ea[i]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+/*
+ * T = 0 spectral function of the bare susceptibility on the grid, all band
+ * pairs (n, m), cube planes [z0, z1):
+ *   S[i] = (V_T/V_G) sum_{tetra, n, m} (oracle_t0_tetra of that tetrahedron),
+ * V_T/V_G = 1/(6 n1 n2 n3). eps[k*nb + n] are the bands at k; epq, if not
+ * NULL, the bands at k + q on the same flat index (epq[k*nb + m] = e_m(k+q));
+ * if NULL they are taken from eps with the integer grid shift q (periodic).
+ */
+int oracle_t0_spectral(int n1, int n2, int n3, int nb, const double *eps, const double *epq,
+                       const int q[3], double mu, int mode, int npts, const double *ea,
+                       const double *eb, int z0, int z1, double *out) {
+    const double vt = 1.0 / (6.0 * (double)n1 * (double)n2 * (double)n3);
+    int x, y, z, t, n, m, v, i;
+    double *acc;
+    if (n1 <= 0 || n2 <= 0 || n3 <= 0 || nb <= 0 || npts < 0 || z0 < 0 || z1 > n3 || z0 > z1) return 1;
+    acc = (double *)calloc((size_t)(npts > 0 ? npts : 1), sizeof(double));
+    if (!acc) return 2;
+    for (z = z0; z < z1; ++z)
+        for (y = 0; y < n2; ++y)
+            for (x = 0; x < n1; ++x)
+                for (t = 0; t < 6; ++t) {
+                    long kk[4], kq[4];
+                    tetra_corners(n1, n2, n3, x, y, z, t, kk);
+                    for (v = 0; v < 4; ++v) {
+                        const long k = kk[v];
+                        const int kx = (int)(k % n1), ky = (int)((k / n1) % n2), kz = (int)(k / ((long)n1 * n2));
+                        const int sx = ((kx + q[0]) % n1 + n1) % n1;
+                        const int sy = ((ky + q[1]) % n2 + n2) % n2;
+                        const int sz = ((kz + q[2]) % n3 + n3) % n3;
+                        kq[v] = epq ? k : (long)sx + (long)n1 * ((long)sy + (long)n2 * sz);
+                    }
+                    for (n = 0; n < nb; ++n)
+                        for (m = 0; m < nb; ++m) {
+                            double a[4], c[4];
+                            const double *src = epq ? epq : eps;
+                            for (v = 0; v < 4; ++v) {
+                                a[v] = eps[kk[v] * nb + n] - mu;
+                                c[v] = src[kq[v] * nb + m] - mu;
+                            }
+                            oracle_t0_tetra(a, c, mode, npts, ea, eb, acc);
+                        }
+                }
+    for (i = 0; i < npts; ++i) out[i] = vt * acc[i];
+    free(acc);
+    return 0;
+}

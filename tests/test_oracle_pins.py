@@ -543,3 +543,189 @@ def test_pair_bands_spectral_weight_integrates_to_zero(q):
     kq = ((x + q[0]) % n1) + n1 * (((y + q[1]) % n2) + n2 * ((z + q[2]) % n3))
     assert d[k, 0 * 2 + 1] == eps[kq, 1] - eps[k, 0]
     assert abs(w[k, 0 * 2 + 1, 0] - (f(eps[k, 0], 0.3, 0.0) - f(eps[kq, 1], 0.3, 0.0))) < 1e-15
+
+
+# ---------------------------------------------------------------- Fermi-Dirac occupation (pair bands)
+def test_fermi_dirac_identities():
+    """f(mu) = 1/2, f(mu + x) + f(mu - x) = 1, f(mu + kT) = 1/(1 + e), limits
+    0 and 1, and f decreasing: the properties that fix the function."""
+    f = oracle.fermi_dirac
+    kT, mu = 0.07, 0.3
+    assert f(mu, kT, mu) == 0.5
+    x = np.linspace(-2, 2, 81)
+    np.testing.assert_allclose(f(mu + x, kT, mu) + f(mu - x, kT, mu), 1.0, atol=1e-15)
+    assert abs(f(mu + kT, kT, mu) - 1.0 / (1.0 + np.e)) < 1e-15
+    assert f(mu + 50, kT, mu) < 1e-300 and f(mu - 50, kT, mu) == 1.0
+    assert np.all(np.diff(f(mu + x, kT, mu)) < 0)
+
+
+def twisted_model(model, q, n):
+    """The model whose H at grid point k is H(k + 2 pi q / n): every hopping
+    t(R) picks up the phase e^{2 pi i q.R / n}, so diagonalising it on the
+    grid gives the bands at k + q without shifting any index."""
+    qf = np.asarray(q, np.float64) / np.asarray(n, np.float64)
+    ph = np.exp(2j * np.pi * (model["R"].astype(np.float64) @ qf))
+    return {"onsite": model["onsite"], "R": model["R"], "t": model["t"] * ph[:, None, None]}
+
+
+def test_pair_bands_shift_k_plus_q_and_sign():
+    """pair_bands at momentum q: the energy is e_m(k + q) - e_n(k) and the
+    weight f(e_n(k)) - f(e_m(k + q)), with the bands at k + q from a separate
+    diagonalisation of H(k + q) (twisted hoppings); the model has no
+    time-reversal symmetry, so k - q would give other values. For w above the
+    largest spread of the transition energy inside any tetrahedron every
+    tetrahedron that contributes has positive transition energy at all
+    corners, hence non-negative weight: S(q, w) >= 0 there (and S <= 0 below
+    minus that spread)."""
+    n = (5, 4, 3)
+    q = (2, 1, 1)
+    model = tbgen.tb_model(7, n_orb=3)
+    eps, _ = oracle.eig(model, *n)
+    epq, _ = oracle.eig(twisted_model(model, q, n), *n)
+    kT, mu = 0.2, float(np.median(eps))
+    d, w = oracle.pair_bands(eps, *n, q, kT, mu)
+    nb = eps.shape[1]
+    for nn in range(nb):
+        for m in range(nb):
+            np.testing.assert_allclose(d[:, nn * nb + m], epq[:, m] - eps[:, nn], atol=1e-11)
+            ref = 0.5 * (np.tanh(0.5 * (epq[:, m] - mu) / kT) - np.tanh(0.5 * (eps[:, nn] - mu) / kT))
+            np.testing.assert_allclose(w[:, nn * nb + m, 0], ref, atol=1e-12)
+    dm, _ = oracle.pair_bands(eps, *n, tuple(-v for v in q), kT, mu)
+    assert np.max(np.abs(dm - d)) > 1e-3   # k - q is distinguishable
+    # sign: spread of the transition energy over each tetrahedron's corners
+    spread = 0.0
+    n1, n2, n3 = n
+    for z in range(n3):
+        for y in range(n2):
+            for x in range(n1):
+                for t in oracle.table_i() - 1:
+                    ks = [((x + (c & 1)) % n1) + n1 * (((y + ((c >> 1) & 1)) % n2) + n2 * ((z + (c >> 2)) % n3))
+                          for c in t]
+                    spread = max(spread, float(np.max(np.ptp(d[ks], axis=0))))
+    E = np.linspace(spread + 1e-6, d.max() + 0.1, 40)
+    s = oracle.dos(d, w, *n, E)[0]
+    assert np.all(s >= -1e-14) and s.max() > 0
+    s_neg = oracle.dos(d, w, *n, -E)[0]
+    assert np.all(s_neg <= 1e-14)
+
+
+# ---------------------------------------------------------------- spectral function at T = 0
+def mc_t0_histogram(a, c, edges, n_samples, seed):
+    """Monte-Carlo estimate of the bin-averaged T = 0 contribution of one
+    tetrahedron (units of V_T/V_G): uniform points (Dirichlet(1,1,1,1)
+    barycentric coordinates), fields a, c interpolated linearly, occupation
+    difference +1 on {a < 0 < c}, -1 on {c < 0 < a}, histogram of c - a."""
+    rng = np.random.default_rng(seed)
+    lam = rng.dirichlet(np.ones(4), size=n_samples)
+    A = lam @ a
+    C = lam @ c
+    wgt = ((A < 0) & (C > 0)).astype(float) - ((A > 0) & (C < 0)).astype(float)
+    h, _ = np.histogram(C - A, bins=edges, weights=wgt)
+    h2, _ = np.histogram(C - A, bins=edges, weights=wgt * wgt)
+    width = np.diff(edges)
+    return h / n_samples / width, np.sqrt(h2) / n_samples / width
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_t0_tetra_against_monte_carlo(seed):
+    """Clipping by both step functions, for random corner values of mixed
+    sign: bin averages against a Monte-Carlo histogram (5 sigma)."""
+    rng = np.random.default_rng(100 + seed)
+    a = rng.normal(0, 1, 4)
+    c = rng.normal(0.2, 1, 4)
+    d = c - a
+    edges = np.linspace(d.min() - 0.05, d.max() + 0.05, 17)
+    s = oracle.spectral_t0_tetra(a, c, edges, mode="bin")
+    mc, sig = mc_t0_histogram(a, c, edges, 2_000_000, seed)
+    assert np.all(np.abs(s - mc) <= 5 * sig + 1e-3), (s, mc, sig)
+
+
+def test_t0_tetra_unclipped_is_the_tetrahedron_density():
+    """All corners occupied in band n and empty in band m: no clipping, the
+    distribution of the transition energy over the whole tetrahedron, i.e.
+    the total of the Sec. II.C corner weight derivatives (oracle.corner_weights,
+    pinned above) divided by V_T/V_G."""
+    a = np.array([-1.0, -0.4, -0.7, -0.2])
+    c = np.array([0.3, 0.9, 0.35, 1.4])
+    d = np.sort(c - a)
+    E = np.linspace(d[0] - 0.1, d[3] + 0.1, 57)
+    s = oracle.spectral_t0_tetra(a, c, E)
+    f = 0.25
+    ref = np.array([oracle.corner_weights(d, x, f)[1].sum() for x in E])
+    np.testing.assert_allclose(s, ref, rtol=1e-12, atol=1e-12)
+    # and band n empty everywhere: nothing
+    assert np.all(oracle.spectral_t0_tetra(-a, c, E) == 0.0)
+
+
+@pytest.mark.parametrize("inside", [1, 3])
+def test_t0_tetra_clipped_volume_closed_form(inside):
+    """Band m empty at every corner, band n occupied at `inside` corners: the
+    total weight (bin mode over every transition energy) is the volume of the
+    occupied part of the tetrahedron, a corner tetrahedron with edge ratios
+    -a_i / (a_j - a_i) (one corner occupied) or the complement of one (three)."""
+    a = np.array([-0.6, 0.5, 0.8, 1.1]) if inside == 1 else np.array([-0.6, -0.5, -0.8, 1.1])
+    c = np.array([0.4, 0.9, 1.3, 2.0])
+    edges = np.linspace(-1, 4, 6)
+    total = (oracle.spectral_t0_tetra(a, c, edges, mode="bin") * np.diff(edges)).sum()
+    if inside == 1:
+        ref = np.prod([-a[0] / (a[j] - a[0]) for j in (1, 2, 3)])
+    else:
+        ref = 1.0 - np.prod([a[3] / (a[3] - a[j]) for j in (0, 1, 2)])
+    assert abs(total - ref) < 1e-13
+
+
+def test_t0_spectral_sign_sum_rule_and_symmetry():
+    """On a periodic grid with a model without time-reversal symmetry:
+    S(q, w) >= 0 for w > 0 and <= 0 for w < 0 (the occupation difference is
+    +1 only where the transition energy is positive); the total weight is
+    zero (the occupied volume of band n and of the shifted band m are equal);
+    S(-q, -w) = -S(q, w) (pairs (n, m) at k and (m, n) at k + q); and the
+    bands at k + q taken from the twisted model give the same S."""
+    n = (4, 3, 3)
+    q = (1, 2, 1)
+    model = tbgen.tb_model(9, n_orb=3)
+    eps, _ = oracle.eig(model, *n)
+    mu = float(np.median(eps))
+    edges = np.linspace(-12, 12, 97)
+    s = oracle.spectral_t0(eps, *n, q, mu, edges, mode="bin")
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    assert np.all(s[mid > 0.13] >= -1e-14) and np.all(s[mid < -0.13] <= 1e-14)
+    assert abs((s * np.diff(edges)).sum()) < 1e-12
+    sm = oracle.spectral_t0(eps, *n, tuple(-v for v in q), mu, -edges[::-1], mode="bin")
+    np.testing.assert_allclose(sm[::-1], -s, atol=1e-13)
+    epq, _ = oracle.eig(twisted_model(model, q, n), *n)
+    st = oracle.spectral_t0(eps, *n, (0, 0, 0), mu, edges, mode="bin", eps_kq=epq)
+    np.testing.assert_allclose(st, s, atol=1e-11)
+    sneg = oracle.spectral_t0(eps, *n, tuple(-v for v in q), mu, edges, mode="bin")
+    assert np.max(np.abs(sneg - s)) > 1e-4 * np.max(np.abs(s))
+
+
+def test_t0_spectral_grid_against_monte_carlo():
+    """Whole-grid bin averages against a Monte-Carlo histogram over all
+    tetrahedra and band pairs (a tiny grid, 2 bands)."""
+    n = (3, 2, 2)
+    n1, n2, n3 = n
+    rng = np.random.default_rng(21)
+    eps = np.sort(rng.normal(0, 1, (n1 * n2 * n3, 2)), axis=1)
+    q, mu = (1, 1, 0), 0.1
+    edges = np.linspace(-5, 5, 21)
+    s = oracle.spectral_t0(eps, *n, q, mu, edges, mode="bin")
+    acc = np.zeros(len(edges) - 1)
+    var = np.zeros(len(edges) - 1)
+    ntet = 6 * n1 * n2 * n3
+    for z in range(n3):
+        for y in range(n2):
+            for x in range(n1):
+                for t in oracle.table_i() - 1:
+                    kk, kq = [], []
+                    for c in t:
+                        xx, yy, zz = (x + (c & 1)) % n1, (y + ((c >> 1) & 1)) % n2, (z + (c >> 2)) % n3
+                        kk.append(xx + n1 * (yy + n2 * zz))
+                        kq.append((xx + q[0]) % n1 + n1 * (((yy + q[1]) % n2) + n2 * ((zz + q[2]) % n3)))
+                    for nn in range(2):
+                        for m in range(2):
+                            h, sg = mc_t0_histogram(eps[kk, nn] - mu, eps[kq, m] - mu, edges, 40_000,
+                                                    len(kk) + 7 * nn + 3 * m + 31 * x + 17 * y + 5 * z)
+                            acc += h / ntet
+                            var += (sg / ntet) ** 2
+    assert np.all(np.abs(s - acc) <= 5 * np.sqrt(var) + 1e-4), np.max(np.abs(s - acc))
