@@ -307,6 +307,36 @@ tetra_status_t tetra_fermi_level(tetra_plan_t plan, const float *eps, const void
 tetra_status_t tetra_pair_bands(tetra_plan_t plan, const float *eps, const int q[3], float kT, float mu,
                                 tetra_plan_t pair_plan, float *eps_pairs, float *w_pairs, cudaStream_t stream);
 
+/* Spectral function of the bare susceptibility at T = 0 (the extension to
+ * susceptibilities the paper names as future work; not in the paper):
+ *   S(q, w) = sum_{n,m} (1/V_G) int dk [Theta(mu - e_n(k)) - Theta(mu - e_m(k+q))]
+ *                                  delta(w - e_m(k+q) + e_n(k)),
+ *   Im chi0(q, w + i0) = -pi S(q, w),
+ * with every band linear inside each tetrahedron (the method's
+ * interpolation) and the step occupations clipped exactly: in each
+ * tetrahedron the regions {e_n < mu < e_m(k+q)} (+1) and
+ * {e_m(k+q) < mu < e_n} (-1) are cut into sub-tetrahedra over which the
+ * transition energy is linear.
+ *   plan    : the bands (n_bands <= 8; n_orb, weight_dtype and mode unused),
+ *             eps in its tetra layout; whole-grid plans only.
+ *   q       : integer grid vector (q_i in units of 2 pi / n_i), any sign.
+ *   mu      : chemical potential (energy units of eps).
+ *   mode    : TETRA_POINT: S at n_omega ascending energies omega[i];
+ *             TETRA_BIN: bin averages over n_omega bins, omega holds the
+ *             n_omega + 1 ascending edges.
+ *   S       : [n_omega] float, overwritten.
+ *   ws      : at least tetra_spectral_t0_workspace_bytes(plan, n_omega)
+ *             bytes, 16-byte aligned.
+ * Exact integer accumulation: the result does not depend on the launch.
+ * Returns TETRA_EINVAL for null/misaligned pointers or a bad mode,
+ * TETRA_EUNSUPPORTED for n_bands > 8, slab plans, or n_omega beyond one
+ * shared-memory tile (about 18000 energies); device-side TETRA_ERANGE
+ * (tetra_workspace_status) for a contribution beyond the 64-bit range. */
+size_t tetra_spectral_t0_workspace_bytes(tetra_plan_t plan, int n_omega);
+tetra_status_t tetra_spectral_t0(tetra_plan_t plan, const float *eps, const int q[3], float mu, int mode,
+                                 int n_omega, const float *omega, float *S, void *ws, size_t ws_bytes,
+                                 cudaStream_t stream);
+
 /* Device-side status recorded in a workspace by the last call that used it
  * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. The
  * fixed-point accumulation of tetra_dos raises TETRA_ERANGE (and leaves that

@@ -77,7 +77,7 @@ def _load():
             lib.oracle_t0_tetra.argtypes = [d, d, i, i, d, d, d]
             lib.oracle_t0_tetra.restype = None
             lib.oracle_t0_spectral.argtypes = [i, i, i, i, d, d, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
-                                               i, i, d, d, i, i, d]
+                                               i, i, d, d, i, i, d, i]
             lib.oracle_t0_spectral.restype = i
             _lib = lib
     return _lib
@@ -356,14 +356,16 @@ def spectral_t0_tetra(a, c, energies, mode="point", edges_hi=None) -> np.ndarray
 
 
 def spectral_t0(eps, n1, n2, n3, q, mu, energies, mode="point", edges_hi=None, eps_kq=None,
-                z_range=None) -> np.ndarray:
+                z_range=None, nthreads: int = 1) -> np.ndarray:
     """T = 0 spectral function of the bare susceptibility,
     S(q, w) = sum_{n,m} (1/V_G) int [Theta(mu - e_n(k)) - Theta(mu - e_m(k+q))]
               delta(w - e_m(k+q) + e_n(k)) dk,   Im chi0(q, w + i0) = -pi S,
     with every band linear inside each tetrahedron and the step occupations
     clipped exactly (C code, ``oracle_t0_spectral``). eps (nk, nb) natural
     layout; eps_kq, if given, holds the bands at k + q on the same flat index
-    (otherwise eps shifted by the integer grid vector q). Returns (npts,)."""
+    (otherwise eps shifted by the integer grid vector q). nthreads > 1 splits
+    the cube planes into contiguous blocks and adds the per-thread results in
+    thread order. Returns (npts,)."""
     lib = _load()
     eps = _c64(eps)
     nk, nb = eps.shape
@@ -374,7 +376,8 @@ def spectral_t0(eps, n1, n2, n3, q, mu, energies, mode="point", edges_hi=None, e
     qa = (ctypes.c_int * 3)(*[int(v) for v in q])
     z0, z1 = (0, n3) if z_range is None else z_range
     rc = lib.oracle_t0_spectral(n1, n2, n3, nb, _p(eps), _p(epq) if epq is not None else None, qa,
-                                float(mu), m, ea.shape[0], _p(ea), _p(eb), int(z0), int(z1), _p(out))
+                                float(mu), m, ea.shape[0], _p(ea), _p(eb), int(z0), int(z1), _p(out),
+                                int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_t0_spectral failed ({rc})")
     return out

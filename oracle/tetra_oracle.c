@@ -573,39 +573,57 @@ void oracle_t0_tetra(const double a[4], const double c[4], int mode, int npts, c
  */
 int oracle_t0_spectral(int n1, int n2, int n3, int nb, const double *eps, const double *epq,
                        const int q[3], double mu, int mode, int npts, const double *ea,
-                       const double *eb, int z0, int z1, double *out) {
+                       const double *eb, int z0, int z1, double *out, int nthreads) {
     const double vt = 1.0 / (6.0 * (double)n1 * (double)n2 * (double)n3);
-    int x, y, z, t, n, m, v, i;
-    double *acc;
+    int i, th;
+    double *part;
     if (n1 <= 0 || n2 <= 0 || n3 <= 0 || nb <= 0 || npts < 0 || z0 < 0 || z1 > n3 || z0 > z1) return 1;
-    acc = (double *)calloc((size_t)(npts > 0 ? npts : 1), sizeof(double));
-    if (!acc) return 2;
-    for (z = z0; z < z1; ++z)
-        for (y = 0; y < n2; ++y)
-            for (x = 0; x < n1; ++x)
-                for (t = 0; t < 6; ++t) {
-                    long kk[4], kq[4];
-                    tetra_corners(n1, n2, n3, x, y, z, t, kk);
-                    for (v = 0; v < 4; ++v) {
-                        const long k = kk[v];
-                        const int kx = (int)(k % n1), ky = (int)((k / n1) % n2), kz = (int)(k / ((long)n1 * n2));
-                        const int sx = ((kx + q[0]) % n1 + n1) % n1;
-                        const int sy = ((ky + q[1]) % n2 + n2) % n2;
-                        const int sz = ((kz + q[2]) % n3 + n3) % n3;
-                        kq[v] = epq ? k : (long)sx + (long)n1 * ((long)sy + (long)n2 * sz);
-                    }
-                    for (n = 0; n < nb; ++n)
-                        for (m = 0; m < nb; ++m) {
-                            double a[4], c[4];
-                            const double *src = epq ? epq : eps;
-                            for (v = 0; v < 4; ++v) {
-                                a[v] = eps[kk[v] * nb + n] - mu;
-                                c[v] = src[kq[v] * nb + m] - mu;
-                            }
-                            oracle_t0_tetra(a, c, mode, npts, ea, eb, acc);
+    if (nthreads < 1) nthreads = 1;
+    part = (double *)calloc((size_t)nthreads * (size_t)(npts > 0 ? npts : 1), sizeof(double));
+    if (!part) return 2;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        int tid = 0, nth = 1, x, y, z, t, n, m, v, zlo, zhi;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+        nth = omp_get_num_threads();
+#endif
+        zlo = z0 + (int)((long)(z1 - z0) * tid / nth);
+        zhi = z0 + (int)((long)(z1 - z0) * (tid + 1) / nth);
+        double *acc = part + (long)tid * (npts > 0 ? npts : 1);
+        for (z = zlo; z < zhi; ++z)
+            for (y = 0; y < n2; ++y)
+                for (x = 0; x < n1; ++x)
+                    for (t = 0; t < 6; ++t) {
+                        long kk[4], kq[4];
+                        tetra_corners(n1, n2, n3, x, y, z, t, kk);
+                        for (v = 0; v < 4; ++v) {
+                            const long k = kk[v];
+                            const int kx = (int)(k % n1), ky = (int)((k / n1) % n2), kz = (int)(k / ((long)n1 * n2));
+                            const int sx = ((kx + q[0]) % n1 + n1) % n1;
+                            const int sy = ((ky + q[1]) % n2 + n2) % n2;
+                            const int sz = ((kz + q[2]) % n3 + n3) % n3;
+                            kq[v] = epq ? k : (long)sx + (long)n1 * ((long)sy + (long)n2 * sz);
                         }
-                }
-    for (i = 0; i < npts; ++i) out[i] = vt * acc[i];
-    free(acc);
+                        for (n = 0; n < nb; ++n)
+                            for (m = 0; m < nb; ++m) {
+                                double a[4], c[4];
+                                const double *src = epq ? epq : eps;
+                                for (v = 0; v < 4; ++v) {
+                                    a[v] = eps[kk[v] * nb + n] - mu;
+                                    c[v] = src[kq[v] * nb + m] - mu;
+                                }
+                                oracle_t0_tetra(a, c, mode, npts, ea, eb, acc);
+                            }
+                    }
+    }
+    for (i = 0; i < npts; ++i) {
+        double sum = 0.0;
+        for (th = 0; th < nthreads; ++th) sum += part[(long)th * npts + i];
+        out[i] = vt * sum;
+    }
+    free(part);
     return 0;
 }

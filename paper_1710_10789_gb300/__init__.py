@@ -28,6 +28,7 @@ __all__ = [
     "EXPORTED_SYMBOLS", "TetraTune", "tetra_plan_batched", "tetra_batch_plan_destroy",
     "tetra_batch_layout", "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
     "BatchPlan", "TETRA_MAX_BATCH", "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
+    "tetra_spectral_t0_workspace_bytes", "tetra_spectral_t0",
 ]
 
 TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
@@ -44,6 +45,7 @@ EXPORTED_SYMBOLS = (
     "tetra_noalloc_status", "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
     "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
     "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
+    "tetra_spectral_t0_workspace_bytes", "tetra_spectral_t0",
 )
 TETRA_MAX_BATCH = 64
 
@@ -130,6 +132,10 @@ def lib():
                                             vp, sz, vp]
             L.tetra_pair_bands.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_float,
                                            ctypes.c_float, vp, vp, vp, vp]
+            L.tetra_spectral_t0_workspace_bytes.argtypes = [vp, i]
+            L.tetra_spectral_t0_workspace_bytes.restype = sz
+            L.tetra_spectral_t0.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_float, i, i, vp, vp,
+                                            vp, sz, vp]
             L.tetra_strerror.argtypes = [i]
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
@@ -138,7 +144,8 @@ def lib():
                          "tetra_dos_backward", "tetra_eig", "tetra_eig_backward",
                          "tetra_workspace_status", "tetra_plan_batched",
                          "tetra_batch_plan_destroy", "tetra_batch_layout", "tetra_batch_info",
-                         "tetra_dos_batched", "tetra_fermi_level", "tetra_pair_bands"):
+                         "tetra_dos_batched", "tetra_fermi_level", "tetra_pair_bands",
+                         "tetra_spectral_t0"):
                 getattr(L, name).restype = i
             _LIB = L
     return _LIB
@@ -190,6 +197,16 @@ def tetra_pair_bands(plan, eps, q, kT, mu, pair_plan, eps_pairs, w_pairs, stream
 def tetra_dos_noalloc(plan, eps, w, omega, dos, stream) -> int:
     """tetra_dos with the library's fixed scratch instead of a workspace (see tetra.h)."""
     return lib().tetra_dos_noalloc(plan, eps, w, omega, dos, stream)
+
+
+def tetra_spectral_t0_workspace_bytes(plan, n_omega) -> int:
+    return int(lib().tetra_spectral_t0_workspace_bytes(plan, int(n_omega)))
+
+
+def tetra_spectral_t0(plan, eps, q, mu, mode, n_omega, omega, S, ws, ws_bytes, stream) -> int:
+    qa = (ctypes.c_int * 3)(*[int(v) for v in q])
+    return lib().tetra_spectral_t0(plan, eps, qa, float(mu), int(mode), int(n_omega), omega, S, ws, ws_bytes,
+                                   stream)
 
 
 def tetra_noalloc_status(device, stream) -> int:
@@ -373,6 +390,27 @@ class Plan:
         _check(tetra_pair_bands(self.handle, _ptr(eps), q, kT, mu, pair_plan.handle, _ptr(eps_p), _ptr(w_p),
                                 _stream_handle(stream)), "tetra_pair_bands")
         return eps_p, w_p
+
+    def spectral_t0(self, eps, q, mu, omega, mode="point", out=None, stream=None):
+        """T = 0 spectral function of the bare susceptibility at grid vector q
+        (tetra_spectral_t0): S at the energies ``omega`` (point mode) or the
+        bin averages between consecutive edges (bin mode). Returns S; its
+        device status is ``spectral_status()``."""
+        torch = _torch()
+        m = _MODES[mode]
+        n_om = omega.numel() - 1 if m == TETRA_BIN else omega.numel()
+        if out is None:
+            out = torch.empty((n_om,), dtype=torch.float32, device=eps.device)
+        nbytes = tetra_spectral_t0_workspace_bytes(self.handle, n_om)
+        if getattr(self, "_spec_ws", None) is None or self._spec_ws.numel() < nbytes:
+            self._spec_ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=eps.device)
+        ws = self._spec_ws
+        _check(tetra_spectral_t0(self.handle, _ptr(eps), q, mu, m, n_om, _ptr(omega), _ptr(out), _ptr(ws),
+                                 ws.numel(), _stream_handle(stream)), "tetra_spectral_t0")
+        return out
+
+    def spectral_status(self, stream=None) -> int:
+        return tetra_workspace_status(_ptr(self._spec_ws), _stream_handle(stream))
 
     def _model(self, params, R):
         n_orb = self.desc.n_bands
