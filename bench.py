@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--mode", default="point", choices=["point", "bin"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e and extra measurements")
-    ap.add_argument("--variant", default=None, choices=["differentiation", "paper_shape", "lindhard", "near_balance"],
+    ap.add_argument("--variant", default=None,
+                    choices=["differentiation", "paper_shape", "lindhard", "spectral_t0", "near_balance"],
                     help="run one extra workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -199,6 +200,40 @@ def alu_roofline(torch, dev, triples, items, ms):
                            "(sm_max_mhz of measured MEASURED_PEAKS.json)",
             "algorithmic": f"{OPS_PER_TRIPLE} FMA-pipe ops x {triples} in-window triples + "
                            f"{OPS_PER_ITEM} x {items} tetra-bands"}
+
+
+def eig_ops_per_point(n_orb=8, n_R=7):
+    """Algorithmic FP32 FMA-pipe operations per k-point of the eigensolver
+    (textbook counts for an n x n complex Hermitian matrix, n = n_orb):
+    H(k) from n_R hopping matrices (4 FMA per upper-triangle entry and R),
+    Householder reduction to tridiagonal form (16/3 n^3 real flops), implicit
+    QR on the real tridiagonal with the rotations accumulated (6 n^3 flops),
+    back-transformation of the eigenvectors by the reflectors (n^3 complex
+    multiply-adds) and the squared moduli (2 n^2)."""
+    n = n_orb
+    h_build = n_R * (n * (n + 1) // 2) * 4
+    tridiag = 16 * n ** 3 // 6
+    qr = 3 * n ** 3
+    back = 4 * n ** 3
+    return h_build + tridiag + qr + back + 2 * n * n
+
+
+def eig_roofline(torch, dev, points, ms):
+    """The eigensolver's algorithmic FP32 throughput against the same FP32 peak."""
+    mp = {}
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = float(mp.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    ops = eig_ops_per_point()
+    ach = 2.0 * ops * points / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "tetra_eig_kernel", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak,
+            "algorithmic": f"{ops} FMA-pipe ops per k-point x {points} padded k-points (H(k), Householder, "
+                           "tridiagonal QR with rotations, back-transformation, |V|^2)"}
 
 
 def time_dos(torch, plan, eps, w, omega, out, steps, warmup):
@@ -534,6 +569,38 @@ def oracle_sample_eigendata(n, planes, seed=0):
     return ev, w
 
 
+def spectral_t0_workload(torch, T, steps, warmup, local):
+    """Spectral function of the bare susceptibility at T = 0 by exact
+    double-band clipping of every tetrahedron (tetra_spectral_t0) on the
+    8-orbital model, 64^3 grid, q = (16, 0, 0), chemical potential at 4
+    electrons per spin, 400 energies on [0, 4] eV (point mode)."""
+    import tbgen
+    dev = torch.device("cuda", local)
+    n = 64
+    p_np, R_np = model_arrays(tbgen.tb_model(0, n_orb=8))
+    plan = T.Plan(n, n, n, 8, 8, 16, device=local)
+    eps, w = plan.eig(torch.from_numpy(p_np).to(dev), torch.from_numpy(R_np).to(dev))
+    mu = plan.fermi_level(eps, w, 4.0)
+    omega = torch.from_numpy(tbgen.uniform_grid(0.0, 4.0, 400)).to(dev)
+    out = torch.empty((400,), dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        plan.spectral_t0(eps, (16, 0, 0), mu, omega, out=out)
+    torch.cuda.synchronize()
+    s_ = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s_)
+    for _ in range(steps):
+        plan.spectral_t0(eps, (16, 0, 0), mu, omega, out=out)
+    b.record(s_)
+    torch.cuda.synchronize()
+    assert plan.spectral_status() == T.TETRA_OK
+    return {"workload": "bare-susceptibility spectral function S(q, w) at T = 0 (exact double-band clipping), "
+                        "8-orbital model, 64^3 grid, q = (16, 0, 0), 64 band pairs, 400 energies on [0, 4] eV",
+            "ms_per_evaluation": a.elapsed_time(b) / steps, "chemical_potential_eV": mu,
+            "spectral_weight_0_to_4eV": float(out.sum()) * 4.0 / 399}
+
+
 def cpu_baseline(n, n_omega, seed=0, planes=None, threads=None, stride=1, omega=None, keep=False):
     """The FP64 oracle on the host cores over a bounded sample of the same
     workload: `planes` cube planes (n x n x planes cubes) of the n^3 grid, all
@@ -677,7 +744,7 @@ def main():
                                       torch.from_numpy(R_np).to(dev), args.steps, args.warmup, local)
         else:
             fn = {"differentiation": differentiation_workload, "paper_shape": paper_shape_workload,
-                  "lindhard": lindhard_workload}[args.variant]
+                  "lindhard": lindhard_workload, "spectral_t0": spectral_t0_workload}[args.variant]
             r = fn(torch, T, args.steps, args.warmup, local)
         if rank == 0:
             print(json.dumps(r), flush=True)
@@ -747,6 +814,7 @@ def main():
     triples = in_window_count(torch, eps, n, 8, omega, args.mode)
     clocks = clk.summary()
     roof = alu_roofline(torch, dev, triples, n_tet * 8, dos_ms)
+    eig_roof = eig_roofline(torch, dev, (n + 1) ** 3, eig_ms)
     roof["traffic"] = dos_traffic(n, nw, args.mode, args.weight_dtype)
     roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 launch "
                               "scaled by boxes (see profiles/)")
@@ -797,6 +865,7 @@ def main():
         if args.mode == "point" and args.weight_dtype == "f32":
             variants["integrated"] = integrated_workload(torch, T, n, eps, w, args.steps, args.warmup, local)
         variants["lindhard"] = lindhard_workload(torch, T, args.steps, args.warmup, local)
+        variants["spectral_t0"] = spectral_t0_workload(torch, T, args.steps, args.warmup, local)
         variants["near_balance"] = near_balance_workload(torch, T, n, params, R, args.steps, args.warmup, local)
     cb = None
     if not args.no_cpu_baseline:
@@ -819,7 +888,7 @@ def main():
         "in_window_updates_per_s": triples / (dos_ms * 1e-3),
         "dense_updates_per_s_dos_only": dense / (dos_ms * 1e-3),
         "in_window_triples": triples,
-        "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks, "variants": variants,
+        "roofline": roof, "eig_roofline": eig_roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks, "variants": variants,
         "gpu_launches": 3 * args.steps,
     }
     print(json.dumps(line), flush=True)

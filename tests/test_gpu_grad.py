@@ -58,6 +58,7 @@ def test_dos_backward_matches_oracle(T, case):
     g = np.random.default_rng(4).normal(0, 1, (w.shape[2], 40))
     ge, gw = run_dos_backward(T, eps, w, n, edges, g)
     re, rw = oracle.dos_bin_grad(eps, w, *n, edges.astype(np.float64), g)
+    print(f"dos backward ({case}): grad_w {rel_err(gw, rw):.2e}, grad_eps {rel_err(ge, re):.2e}")
     assert rel_err(gw, rw) < 2e-5
     assert rel_err(ge, re) < 5e-4
 
@@ -80,7 +81,9 @@ def test_eig_backward_matches_oracle(T):
     torch.cuda.synchronize()
     ref = oracle.eig_backward(m64, *n, geps, gw)
     # FP32 eigenvectors: compare against the largest entry
-    assert rel_err(g.cpu().numpy().astype(np.float64), ref) < 2e-3
+    err = rel_err(g.cpu().numpy().astype(np.float64), ref)
+    print(f"eig backward: {err:.2e}")
+    assert err < 2e-3
 
 
 def chain_loss_oracle(params, model, n, edges, target):
@@ -90,12 +93,22 @@ def chain_loss_oracle(params, model, n, edges, target):
     return float(((d - target) ** 2).sum())
 
 
-@pytest.mark.parametrize("n,nbins,ndir", [((10, 10, 10), 120, 3), ((64, 64, 64), 200, 1)])
-def test_hopping_gradient_through_the_chain(T, n, nbins, ndir):
-    """Config 'differentiation': loss = sum (bin DOS - target)^2 with the target
-    from a second seeded model; gradient with respect to the 150 fitted real
-    parameters vs central differences of the FP64 oracle chain along random
-    directions in that subset."""
+# Error budget of the chain gradient: the
+# FP32 eigensolver adjoint is good to 2e-3 of the largest entry of the
+# parameter gradient (test_eig_backward_matches_oracle); the FP32 forward
+# DOS (2e-5 of its maximum) and the DOS adjoint (2e-5 for the weights, 5e-4
+# for the energies) add less. Every component of the chain gradient is
+# therefore within CHAIN_TOL * max|gradient| of the exact one, and a
+# directional derivative g.v (|v| = 1) within CHAIN_TOL * |g_subset|_2. The
+# finite differences of the FP64 oracle chain carry their own error: the loss
+# is only once continuously differentiable (its second derivative jumps when
+# a corner energy crosses a bin edge or a case boundary), so the central
+# difference is compared with Richardson's extrapolation from steps h and h/2
+# and their difference is added to the bound.
+CHAIN_TOL = 3e-3
+
+
+def chain_setup(T, n, nbins):
     from paper_1710_10789_gb300.autograd import model_dos
 
     model = tbgen.tb_model(0, n_orb=8)
@@ -114,14 +127,52 @@ def test_hopping_gradient_through_the_chain(T, n, nbins, ndir):
     loss = ((dos.double() - torch.from_numpy(target).to(dev)) ** 2).sum()
     loss.backward()
     grad = params.grad.cpu().numpy().astype(np.float64)
-    p64 = p32.astype(np.float64)
+    return model, p32.astype(np.float64), idx, grad, e64, target
+
+
+def richardson(f, h):
+    """Central difference of f at 0 with steps h and h/2: (extrapolated value,
+    error estimate)."""
+    d1 = (f(h) - f(-h)) / (2 * h)
+    d2 = (f(h / 2) - f(-h / 2)) / h
+    return (4 * d2 - d1) / 3, abs(d2 - d1)
+
+
+@pytest.mark.parametrize("n,nbins", [((10, 10, 10), 120), ((64, 64, 64), 200)])
+def test_hopping_gradient_through_the_chain(T, n, nbins):
+    """Config 'differentiation': loss = sum (bin DOS - target)^2 with the target
+    from a second seeded model; gradient with respect to the 150 fitted real
+    parameters against finite differences of the FP64 oracle chain along four
+    random directions in that subset."""
+    model, p64, idx, grad, e64, target = chain_setup(T, n, nbins)
+    gnorm = np.linalg.norm(grad[idx])
     rng = np.random.default_rng(11)
-    h = 1e-4
-    for _ in range(ndir):
+    worst = 0.0
+    for _ in range(4):
         v = np.zeros_like(p64)
         v[idx] = rng.normal(0, 1, idx.size)
         v /= np.linalg.norm(v)
-        fd = (chain_loss_oracle(p64 + h * v, model, n, e64, target) -
-              chain_loss_oracle(p64 - h * v, model, n, e64, target)) / (2 * h)
+        fd, fd_err = richardson(lambda h: chain_loss_oracle(p64 + h * v, model, n, e64, target), 2e-4)
         an = float(grad @ v)
-        assert abs(an - fd) <= 2e-2 * abs(fd) + 1e-6, (an, fd)
+        worst = max(worst, (abs(an - fd) - fd_err) / gnorm)
+        assert abs(an - fd) <= CHAIN_TOL * gnorm + fd_err, (an, fd, fd_err, gnorm)
+    print(f"chain {n}: max |g.v - FD| / |g| = {max(worst, 0.0):.2e} (bound {CHAIN_TOL})")
+
+
+def test_full_parameter_gradient_16cube(T):
+    """Every one of the 150 fitted parameters, 16^3 grid, 200 bins: the GPU
+    chain gradient against the FP64 oracle chain's central differences
+    (Richardson-extrapolated), component by component."""
+    n = (16, 16, 16)
+    model, p64, idx, grad, e64, target = chain_setup(T, n, 200)
+    fd = np.zeros(idx.size)
+    fd_err = np.zeros(idx.size)
+    for j, i in enumerate(idx):
+        e = np.zeros_like(p64)
+        e[i] = 1.0
+        fd[j], fd_err[j] = richardson(lambda h: chain_loss_oracle(p64 + h * e, model, n, e64, target), 2e-4)
+    scale = np.max(np.abs(fd))
+    err = np.abs(grad[idx] - fd)
+    print(f"16^3 full gradient, 150 parameters: max |g - FD| / max|FD| = {np.max(err) / scale:.2e}, "
+          f"max FD error estimate / max|FD| = {np.max(fd_err) / scale:.2e}")
+    assert np.all(err <= CHAIN_TOL * scale + fd_err), np.max(err) / scale
