@@ -288,6 +288,11 @@ __global__ void __launch_bounds__(kSpecThreads)
     // V_T/V_G in fixed-point units: de * 2^26
     const float scale = (float)ldexp(mean_spacing(om, n_om, mode), kSpecBits);
     const SpecArgs S{om, tile, n_om, mode, scale, status};
+    // energy range of the grid: a band pair whose transition energies over a
+    // tetrahedron miss it contributes nothing (the clipped regions' values
+    // lie between the corner minimum and maximum); the +1 region has positive
+    // transition energies, the -1 region negative ones
+    const float om_lo = om[0], om_hi = om[n_edges - 1];
     const long n_items = 6L * n1 * n2 * (long)(z1 - z0);
     for (long it = blockIdx.x * (long)blockDim.x + threadIdx.x; it < n_items; it += (long)gridDim.x * blockDim.x) {
         const int t = (int)(it % 6);
@@ -331,8 +336,15 @@ __global__ void __launch_bounds__(kSpecThreads)
         for (int n = 0; n < NB; ++n) {
 #pragma unroll
             for (int m = 0; m < NB; ++m) {
-                const bool plus = ((an >> n) & 1u) && ((cp >> m) & 1u);
-                const bool minus = ((ap >> n) & 1u) && ((cn >> m) & 1u);
+                bool plus = ((an >> n) & 1u) && ((cp >> m) & 1u);
+                bool minus = ((ap >> n) & 1u) && ((cn >> m) & 1u);
+                if (!plus && !minus) continue;
+                const float d0 = c[0][m] - a[0][n], d1 = c[1][m] - a[1][n];
+                const float d2 = c[2][m] - a[2][n], d3 = c[3][m] - a[3][n];
+                const float dlo = fminf(fminf(d0, d1), fminf(d2, d3)), dhi = fmaxf(fmaxf(d0, d1), fmaxf(d2, d3));
+                if (dhi < om_lo || dlo > om_hi) continue;
+                plus = plus && om_hi > 0.f;
+                minus = minus && om_lo < 0.f;
                 if (!plus && !minus) continue;
                 const P5 v0{1.f, 0.f, 0.f, a[0][n], c[0][m]};
                 const P5 v1{0.f, 1.f, 0.f, a[1][n], c[1][m]};
