@@ -181,6 +181,16 @@ __device__ __forceinline__ float item_dither(uint32_t key) {
     return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
 }
 
+// floor(a / d) for 0 <= a and 0 < d below 2^24: a float quotient corrected
+// by one step (the TMA issue at the end of a box sits on every thread's path
+// to the next barrier, so it avoids integer division).
+__device__ __forceinline__ int fdivq(int a, int d) {
+    int q = (int)__fdividef((float)a, (float)d);
+    q -= (q * d > a) ? 1 : 0;
+    q += ((q + 1) * d <= a) ? 1 : 0;
+    return q;
+}
+
 __device__ __forceinline__ float safe_rcp(float x) { return x > 0.f ? __fdividef(1.0f, x) : 0.f; }
 
 // Per-item constants of the weight formulas, in fixed-point units.
@@ -211,8 +221,10 @@ __device__ __forceinline__ void tet_setup(Tet &T, float e1, float e2, float e3, 
 //    g (3 - v S) and the other three g v / E_j1 (or g v / E_4j);
 //  * in E2 < E <= E3 every dw_l is a cubic in t = E - E2, evaluated by
 //    Horner from coefficients expanded from the printed C1, C2, C3 forms.
+// e2c is the upper end of the first case: E2, or the float just below E4 when
+// E2 = E4 (then no energy below E4 may take the first case's form).
 struct TetP {
-    float e1, e2, e3, e4;
+    float e1, e2, e3, e4, e2c;
     float P1, S1, r21, r31, r41;
     float P3, S3, r42, r43;
     float c[4][4];   // c[l][m]: coefficient of t^m in dw_l (case E2 < E <= E3)
@@ -220,6 +232,7 @@ struct TetP {
 
 __device__ __forceinline__ void tetp_setup(TetP &T, float e1, float e2, float e3, float e4, float fq) {
     T.e1 = e1; T.e2 = e2; T.e3 = e3; T.e4 = e4;
+    T.e2c = (e2 < e4) ? e2 : nextafterf(e4, -INFINITY);
     const float A = e2 - e1, B = e3 - e2, C = e4 - e2;
     T.r21 = safe_rcp(A); T.r31 = safe_rcp(e3 - e1); T.r41 = safe_rcp(e4 - e1);
     const float r32 = safe_rcp(B);
@@ -257,27 +270,34 @@ __device__ __forceinline__ void tetp_setup(TetP &T, float e1, float e2, float e3
 
 // Valid at any E: outside (E1, E4) the clamped distance v = 0 makes every
 // derivative exactly zero (E >= E4 always takes the E4 - E form). At E = E3
-// the third case's form is used (equal to the second's by continuity).
+// the third case's form is used (equal to the second's by continuity). The
+// two mirrored forms give, in sorted corner order, (apex, u r21, u r31, u r41)
+// for the first case and (u r41, u r42, u r43, apex) for the third, so the
+// first and last outputs swap apex and u r41 and the middle two pick their
+// reciprocal: fewer selects than choosing every parameter first.
 __device__ __forceinline__ void tetp_dw(const TetP &T, float E, float d[4]) {
-    const bool in1 = E <= T.e2 && E < T.e4;
+    const bool in1 = E <= T.e2c;
     const bool in3 = !in1 && E >= T.e3;
     const float v = fmaxf(in1 ? E - T.e1 : T.e4 - E, 0.f);
     const float P = in1 ? T.P1 : T.P3;
     const float S = in1 ? T.S1 : T.S3;
-    const float ra = in1 ? T.r21 : T.r41, rb = in1 ? T.r31 : T.r42, rc = in1 ? T.r41 : T.r43;
     const float g = P * v * v;
     const float apex = g * fmaf(-v, S, 3.f);
     const float u = g * v;
-    const float o1 = u * ra, o2 = u * rb, o3 = u * rc;
+    const float u41 = u * T.r41;
+    const float m0 = in1 ? apex : u41;
+    const float m1 = u * (in1 ? T.r21 : T.r42);
+    const float m2 = u * (in1 ? T.r31 : T.r43);
+    const float m3 = in1 ? u41 : apex;
     const float t = E - T.e2;
     float h[4];
 #pragma unroll
     for (int l = 0; l < 4; ++l) h[l] = fmaf(fmaf(fmaf(T.c[l][3], t, T.c[l][2]), t, T.c[l][1]), t, T.c[l][0]);
     const bool in2 = !in1 && !in3;
-    d[0] = in2 ? h[0] : (in1 ? apex : o1);
-    d[1] = in2 ? h[1] : (in1 ? o1 : o2);
-    d[2] = in2 ? h[2] : (in1 ? o2 : o3);
-    d[3] = in2 ? h[3] : (in1 ? o3 : apex);
+    d[0] = in2 ? h[0] : m0;
+    d[1] = in2 ? h[1] : m1;
+    d[2] = in2 ? h[2] : m2;
+    d[3] = in2 ? h[3] : m3;
 }
 
 // w_l(E) for any E (Sec. II.C, all five cases), sorted corners.
@@ -485,7 +505,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         int mi, box;
         if (!work(k, mi, box)) return;
         const ModelP &Mk = B.m[mi];
-        const int ix = box % Mk.nbx, iy = (box / Mk.nbx) % Mk.nby, iz = box / (Mk.nbx * Mk.nby);
+        const int bq = fdivq(box, Mk.nbx), iz = fdivq(bq, Mk.nby), ix = box - bq * Mk.nbx, iy = bq - iz * Mk.nby;
         ++n_issued[stg];
         mbar_arrive_expect_tx(&mbar[stg], A.e_box_bytes);
         tma_load_4d(estage[stg], &B.maps[mi].e, 0, ix * A.BX, iy * A.BY, Mk.z0 + iz * A.BZ, &mbar[stg]);
@@ -495,7 +515,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         int mi, box;
         if (!work(k, mi, box)) return;
         const ModelP &Mk = B.m[mi];
-        const int ix = box % Mk.nbx, iy = (box / Mk.nbx) % Mk.nby, iz = box / (Mk.nbx * Mk.nby);
+        const int bq = fdivq(box, Mk.nbx), iz = fdivq(bq, Mk.nby), ix = box - bq * Mk.nbx, iy = bq - iz * Mk.nby;
         ++n_issued[2];
         mbar_arrive_expect_tx(&mbar[2], A.w_box_bytes);
         tma_load_4d(wstage, &B.maps[mi].w, 0, ix * A.BX, iy * A.BY, Mk.z0 + iz * A.BZ, &mbar[2]);
@@ -662,41 +682,61 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         // of its length K, so that pass B can hand items of similar length to
         // the same warp. The integers an item adds do not depend on which thread
         // adds them, so the grouping cannot change the result.
-        for (int base = warp * 32; base < A.items_per_box; base += nwarp * 32) {
-            const int it = base + lane;
-            // integrated mode: an item also counts when only its step (the first
-            // energy at or above E4) lies in the chunk; items off the grid get
-            // lo = w0 + wc, which makes them inactive
-            int K = 0, lo = (MODE == TETRA_INTEGRATED) ? w0 + wc : 0;
-            if (it < A.items_per_box) {
-                constexpr bool PAIRS = Cfg<MODE, NORB>::pairs;
-                constexpr int UPC = Cfg<MODE, NORB>::units_per_cube;
-                const int cube = it & (ncube - 1);
-                const int rest = it >> lcube;
-                const int t = rest % UPC, n = rest / UPC;
-                const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
-                if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
-                    // a pair's window is the union of its two tetrahedra's: the
-                    // window of the min / max over its five corners
-                    float e1 = 3.0e38f, e4 = -3.0e38f;
-                    const uint32_t code = PAIRS ? pair_code(t) : tet_code(t);
-                    const int p0 = cx + PX * (cy + PY * cz);
+        // Each thread takes up to four items at once: their windows are
+        // independent, so the corner loads and window searches of the four
+        // overlap instead of running one after another.
+        {
+            constexpr int U = 4;
+            const int stride_w = nwarp * 32;
+            for (int base0 = warp * 32; base0 < A.items_per_box; base0 += stride_w * U) {
+                int Ku[U], lou[U];
 #pragma unroll
-                    for (int q = 0; q < (PAIRS ? 5 : 4); ++q) {
-                        const int p = p0 + s_cdelta[(code >> (3 * q)) & 7];
-                        const float ev = Es[p * A.eps_stride + n];
-                        e1 = fminf(e1, ev);
-                        e4 = fmaxf(e4, ev);
+                for (int uu = 0; uu < U; ++uu) {
+                    const int it = base0 + uu * stride_w + lane;
+                    // integrated mode: an item also counts when only its step (the
+                    // first energy at or above E4) lies in the chunk; items off the
+                    // grid get lo = w0 + wc, which makes them inactive
+                    int K = 0, lo = (MODE == TETRA_INTEGRATED) ? w0 + wc : 0;
+                    if (it < A.items_per_box) {
+                        constexpr bool PAIRS = Cfg<MODE, NORB>::pairs;
+                        constexpr int UPC = Cfg<MODE, NORB>::units_per_cube;
+                        const int cube = it & (ncube - 1);
+                        const int rest = it >> lcube;
+                        const int t = rest % UPC, n = rest / UPC;
+                        const int cx = cube & (A.BX - 1), cy = (cube >> A.lbx) & (A.BY - 1), cz = cube >> (A.lbx + A.lby);
+                        if (gx0 + cx < M.n1 && gy0 + cy < M.n2 && gz0 + cz < M.z1) {
+                            // a pair's window is the union of its two tetrahedra's:
+                            // the window of the min / max over its five corners
+                            float e1 = 3.0e38f, e4 = -3.0e38f;
+                            const uint32_t code = PAIRS ? pair_code(t) : tet_code(t);
+                            const int p0 = cx + PX * (cy + PY * cz);
+#pragma unroll
+                            for (int q = 0; q < (PAIRS ? 5 : 4); ++q) {
+                                const int p = p0 + s_cdelta[(code >> (3 * q)) & 7];
+                                const float ev = Es[p * A.eps_stride + n];
+                                e1 = fminf(e1, ev);
+                                e4 = fmaxf(e4, ev);
+                            }
+                            int hi;
+                            item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, M.n_omega, lo, hi);
+                            K = max(0, hi - lo + 1);
+                        }
                     }
-                    int hi;
-                    item_window<MODE>(e1, e4, om, w0, wc, om0, inv_de, M.n_omega, lo, hi);
-                    K = max(0, hi - lo + 1);
+                    Ku[uu] = K;
+                    lou[uu] = lo;
                 }
-                s_lo[it] = (short)(lo - w0);
-                s_K[it] = (unsigned short)K;
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                    const int it = base0 + uu * stride_w + lane;
+                    const int K = Ku[uu], lo = lou[uu];
+                    if (it < A.items_per_box) {
+                        s_lo[it] = (short)(lo - w0);
+                        s_K[it] = (unsigned short)K;
+                    }
+                    const bool act = it < A.items_per_box && (K > 0 || (MODE == TETRA_INTEGRATED && lo + K < w0 + wc));
+                    if (act) atomicAdd(&khist[min(K, kKBins - 1)], 1);
+                }
             }
-            const bool act = K > 0 || (MODE == TETRA_INTEGRATED && lo + K < w0 + wc);
-            if (act) atomicAdd(&khist[min(K, kKBins - 1)], 1);
         }
         __syncthreads();
         // Items ranked by window length K: an exclusive scan of the K histogram
