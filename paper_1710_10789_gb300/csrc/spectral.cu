@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kSpecThreads)
         }
         // per band: some corner occupied (an), some corner empty (ap); the
         // same for the bands at k + q (cn: occupied, cp: empty)
-        uint32_t an = 0, ap = 0, cn = 0, cp = 0;
+        uint32_t an = 0, ap = 0, cn = 0, cp = 0, a_all = 0, c_all = 0;
 #pragma unroll
         for (int n = 0; n < NB; ++n) {
             const float amin = fminf(fminf(a[0][n], a[1][n]), fminf(a[2][n], a[3][n]));
@@ -331,6 +331,8 @@ __global__ void __launch_bounds__(kSpecThreads)
             ap |= (amax > 0.f ? 1u : 0u) << n;
             cn |= (cmin < 0.f ? 1u : 0u) << n;
             cp |= (cmax > 0.f ? 1u : 0u) << n;
+            a_all |= (amax < 0.f ? 1u : 0u) << n;   // occupied at every corner
+            c_all |= (cmin > 0.f ? 1u : 0u) << n;   // empty at every corner
         }
 #pragma unroll
         for (int n = 0; n < NB; ++n) {
@@ -351,6 +353,13 @@ __global__ void __launch_bounds__(kSpecThreads)
                 const P5 v2{0.f, 0.f, 1.f, a[2][n], c[2][m]};
                 const P5 v3{0.f, 0.f, 0.f, a[3][n], c[3][m]};
                 const uint32_t key = ((uint32_t)it * (uint32_t)(NB * NB) + (uint32_t)(n * NB + m)) * 2u;
+                // band n occupied and band m empty at every corner: the +1
+                // region is the whole tetrahedron (the same sub-tetrahedron and
+                // dither key the two cuts would produce)
+                if (((a_all >> n) & 1u) && ((c_all >> m) & 1u)) {
+                    accumulate(v0, v1, v2, v3, 1.f, key * 16u, S);
+                    continue;
+                }
                 // +1 on {a < 0, c > 0}; -1 on {a > 0, c < 0}
                 if (plus) region(v0, v1, v2, v3, 0, 3, 1.f, key, S);
                 if (minus) region(v0, v1, v2, v3, 1, 2, -1.f, key + 1u, S);
