@@ -18,6 +18,12 @@
 // corner sums to the gradient arrays without atomics. A last pass folds the
 // periodic images onto the interior points. Every sum runs in a fixed order,
 // so the result is deterministic.
+//
+// The kernel is bound by the latency of its loads and branches, not by its
+// arithmetic: three blocks per SM (168 registers) hide more of it than two.
+// To fit that register count, the third weight case runs through the first
+// case's code on the mirrored tetrahedron, which also keeps a warp whose
+// lanes sit in both outer cases on one path.
 #include "tetra_internal.cuh"
 
 namespace tetra {
@@ -86,16 +92,7 @@ __device__ __forceinline__ void weights4(const TetD &T, float E, float f, F4 w[4
     } else if (E >= T.e4.v) {
 #pragma unroll
         for (int l = 0; l < 4; ++l) w[l] = konst(f);
-    } else if (E <= T.e2.v) {
-        const F4 x = konst(E) - T.e1;
-        const F4 C = f * (((x * x) * x) * ((T.r21 * T.r31) * T.r41));
-        const F4 S = T.r21 + T.r31 + T.r41;
-        const F4 Cx = C * x;
-        w[0] = C * (4.f - x * S);
-        w[1] = Cx * T.r21;
-        w[2] = Cx * T.r31;
-        w[3] = Cx * T.r41;
-    } else if (E <= T.e3.v) {
+    } else if (E > T.e2.v && E <= T.e3.v) {
         const F4 a = konst(E) - T.e1, bq = konst(E) - T.e2, c = T.e3 - konst(E), dd = T.e4 - konst(E);
         const F4 r3141 = T.r31 * T.r41;
         const F4 C1 = f * ((a * a) * r3141);
@@ -107,14 +104,21 @@ __device__ __forceinline__ void weights4(const TetD &T, float E, float f, F4 w[4
         w[2] = (C12 * a) * T.r31 + (C23 * bq) * T.r32;
         w[3] = (C123 * a) * T.r41 + (C3 * bq) * T.r42;
     } else {
-        const F4 y = T.e4 - konst(E);
-        const F4 C = f * (((y * y) * y) * ((T.r41 * T.r42) * T.r43));
-        const F4 S = T.r41 + T.r42 + T.r43;
-        const F4 Cy = C * y;
-        w[0] = f - Cy * T.r41;
-        w[1] = f - Cy * T.r42;
-        w[2] = f - Cy * T.r43;
-        w[3] = f - C * (4.f - S * y);
+        // E1 < E <= E2, or E3 < E < E4 as the first case of the mirrored
+        // tetrahedron (energies -E4 <= -E3 <= -E2 <= -E1 at -E: distance
+        // E4 - E, reciprocals 1/E43, 1/E42, 1/E41), whose weights are f minus
+        // the original's in reverse corner order
+        const bool mir = E > T.e2.v;
+        const F4 x = mir ? T.e4 - konst(E) : konst(E) - T.e1;
+        const F4 ra = mir ? T.r43 : T.r21, rb = mir ? T.r42 : T.r31;
+        const F4 C = f * (((x * x) * x) * ((ra * rb) * T.r41));
+        const F4 S = ra + rb + T.r41;
+        const F4 Cx = C * x;
+        const F4 u0 = C * (4.f - x * S), u1 = Cx * ra, u2 = Cx * rb, u3 = Cx * T.r41;
+        w[0] = mir ? f - u3 : u0;
+        w[1] = mir ? f - u2 : u1;
+        w[2] = mir ? f - u1 : u2;
+        w[3] = mir ? f - u0 : u3;
     }
 }
 
@@ -146,7 +150,7 @@ inline size_t bwd_stage_bytes(int n_orb, int n_bins) {
 inline size_t bwd_scratch_bytes(int n_orb) { return sizeof(float) * (1 + (size_t)n_orb) * 8 * kBwdThreads; }
 
 template <int NORB, typename WT>
-__global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArgs A, int px, int py, int pz) {
+__global__ void __launch_bounds__(kBwdThreads, 3) tetra_dos_bwd_kernel(const BwdArgs A, int px, int py, int pz) {
     extern __shared__ float s_mem[];
     const int ng = A.n_orb * A.n_bins;
     const size_t stage = A.staged ? (size_t)ng + 2 * (size_t)A.n_bins + 1 : 0;
@@ -269,14 +273,23 @@ __global__ void __launch_bounds__(kBwdThreads) tetra_dos_bwd_kernel(const BwdArg
 // Folds the periodic images (x = n1, y = n2, z = n3 in the padded layout) onto
 // the interior point they copy and zeroes them: one thread per (interior
 // point on a face x = 0, y = 0 or z = 0, band), images added in a fixed order.
+// The face points are enumerated plane by plane: x = 0; y = 0 with x >= 1;
+// z = 0 with x, y >= 1.
 __global__ void tetra_dos_bwd_fold(const BwdArgs A) {
-    const long pts = (long)A.n1 * A.n2 * A.n3;
+    const long fa = (long)A.n2 * A.n3, fb = (long)(A.n1 - 1) * A.n3, fc = (long)(A.n1 - 1) * (A.n2 - 1);
     const long gid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (gid >= pts * A.nb) return;
+    if (gid >= (fa + fb + fc) * A.nb) return;
     const int n = (int)(gid % A.nb);
-    const long k = gid / A.nb;
-    const int x = (int)(k % A.n1), y = (int)((k / A.n1) % A.n2), z = (int)(k / ((long)A.n1 * A.n2));
-    if (x != 0 && y != 0 && z != 0) return;
+    long k = gid / A.nb;
+    int x, y, z;
+    if (k < fa) {                      // plane x = 0
+        x = 0; y = (int)(k % A.n2); z = (int)(k / A.n2);
+    } else if ((k -= fa) < fb) {       // plane y = 0, x >= 1
+        x = 1 + (int)(k % (A.n1 - 1)); y = 0; z = (int)(k / (A.n1 - 1));
+    } else {                           // plane z = 0, x, y >= 1
+        k -= fb;
+        x = 1 + (int)(k % (A.n1 - 1)); y = 1 + (int)(k / (A.n1 - 1)); z = 0;
+    }
     const int mx = x == 0 ? 2 : 1, my = y == 0 ? 2 : 1, mz = z == 0 ? 2 : 1;
     const long p0 = x + (long)A.nx * (y + (long)A.ny * z);
     float se = A.geps[p0 * A.eps_stride + n];
@@ -321,8 +334,8 @@ cudaError_t launch_bwd_n(const Plan &P, const BwdArgs &A, cudaStream_t stream) {
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
-        const long pts = (long)A.n1 * A.n2 * A.n3 * A.nb;
-        tetra_dos_bwd_fold<<<(int)((pts + 255) / 256), 256, 0, stream>>>(A);
+        const long face = ((long)A.n2 * A.n3 + (long)(A.n1 - 1) * A.n3 + (long)(A.n1 - 1) * (A.n2 - 1)) * A.nb;
+        tetra_dos_bwd_fold<<<(int)((face + 255) / 256), 256, 0, stream>>>(A);
         return cudaGetLastError();
     };
     switch (P.d.weight_dtype) {
