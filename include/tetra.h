@@ -333,7 +333,7 @@ tetra_status_t tetra_pair_bands(tetra_plan_t plan, const float *eps, const int q
  * Exact integer accumulation: the result does not depend on the launch.
  * Returns TETRA_EINVAL for null/misaligned pointers or a bad mode,
  * TETRA_EUNSUPPORTED for n_bands > 8, slab plans, or n_omega beyond one
- * shared-memory tile (about 18000 energies); device-side TETRA_ERANGE
+ * shared-memory tile (about 17000 energies); device-side TETRA_ERANGE
  * (tetra_workspace_status) for a contribution beyond the 64-bit range. */
 size_t tetra_spectral_t0_workspace_bytes(tetra_plan_t plan, int n_omega);
 tetra_status_t tetra_spectral_t0(tetra_plan_t plan, const float *eps, const int q[3], float mu, int mode,

@@ -18,14 +18,20 @@
 // a tetrahedron (the total of Sec. II.C's corner weight derivatives divided
 // by V_T / V_G), or nu * [G(w_hi) - G(w_lo)] / (w_hi - w_lo) as a bin average.
 //
-// One thread per (cube, tetrahedron) runs over the band pairs; a pair whose
-// regions are empty (band n nowhere occupied or band m nowhere empty for the
-// +1 region, and the converse for -1) is skipped from four corner minima and
-// maxima. Contributions are rounded once to integers of a fixed-point unit
+// One thread per (cube, tetrahedron) runs over the band pairs in a loop that
+// is not unrolled (the unrolled 64-pair loop overflowed the instruction
+// cache); a pair whose regions are empty (band n nowhere occupied or band m
+// nowhere empty for the +1 region, and the converse for -1) is skipped from
+// four corner minima and maxima. The clipping only queues the kept
+// sub-tetrahedra (sorted transition energies, amplitude, dither key) in a
+// per-warp queue in shared memory; between band pairs, once the queue holds
+// kDrainAt entries, all 32 lanes drain it, one sub-tetrahedron per lane, so
+// the per-energy work is not serialised behind the lanes' different clip
+// paths. Contributions are rounded once to integers of a fixed-point unit
 // (a dither hashed from the contribution's identity makes the rounding
 // unbiased) and added with 64-bit integer atomics into a per-CTA shared
 // tile, then summed over CTAs in fixed order: the result does not depend on
-// the schedule.
+// the schedule or on the order in which queues are drained.
 #include <atomic>
 
 #include "tetra_internal.cuh"
@@ -34,8 +40,12 @@ namespace tetra {
 
 namespace {
 
-constexpr int kSpecThreads = 256;
+constexpr int kSpecThreads = 128;
+constexpr int kSpecWarps = kSpecThreads / 32;
+constexpr int kSpecBlocksPerSM = 4;
 constexpr int kSpecBits = 26;   // fixed-point fraction bits of the unit below
+constexpr int kQueueCap = 256;  // sub-tetrahedra per warp queue
+constexpr int kDrainAt = 64;    // a queue this full is drained before the next band pair
 
 // Table I (corner labels minus one, label c at offset (c&1, (c>>1)&1, (c>>2)&1)).
 __constant__ int kSpecTable[6][4] = {{0, 1, 2, 5}, {1, 2, 3, 5}, {0, 2, 4, 5},
@@ -70,6 +80,13 @@ __device__ __forceinline__ void cswap5(P5 &x, P5 &y, float &sx, float &sy) {
     }
 }
 
+// One sub-tetrahedron waiting in a warp's queue: its sorted transition
+// energies, amplitude sign * nu * scale and dither key.
+struct SubTet {
+    float d0, d1, d2, d3, amp;
+    uint32_t key;
+};
+
 // Constants of a launch that the sub-tetrahedron accumulation needs.
 struct SpecArgs {
     const float *om;        // shared: energies (point) or bin edges (bin)
@@ -78,6 +95,10 @@ struct SpecArgs {
     int mode;               // TETRA_POINT or TETRA_BIN
     float scale;            // V_T/V_G over the fixed-point unit
     int *status;
+    float om0, om_last;     // first and last grid energy (edge)
+    float inv_de;           // 1 / mean spacing, for the index estimates
+    SubTet *q;              // shared: this warp's queue [kQueueCap]
+    int *qn;                // shared: its fill count
 };
 
 // Normalised density g and cumulative G of a linear function with sorted
@@ -88,33 +109,24 @@ struct Lin {
     float g2c;                     // G case 2: (d21^2 + 3 d21 x + 3 x^2 - k2b x^3) * g2c
 };
 
+// (All three pieces are evaluated and one is selected: the lanes of a warp
+// walk different sub-tetrahedra, so a branch per piece would diverge.)
 __device__ __forceinline__ float lin_g(const Lin &L, float w) {
-    if (!(w > L.d0) || !(w < L.d3)) return 0.f;
-    if (w <= L.d1) {
-        const float x = w - L.d0;
-        return L.k1 * x * x;
-    }
-    if (w <= L.d2) {
-        const float x = w - L.d1;
-        return L.k2a * fmaf(-L.k2b * x, x, fmaf(2.f, x, L.d1 - L.d0));
-    }
-    const float y = L.d3 - w;
-    return L.k3 * y * y;
+    const float x1 = w - L.d0, x2 = w - L.d1, y = L.d3 - w;
+    const float g1 = L.k1 * x1 * x1;
+    const float g2 = L.k2a * fmaf(-L.k2b * x2, x2, fmaf(2.f, x2, L.d1 - L.d0));
+    const float g3 = L.k3 * y * y;
+    const float g = (w <= L.d1) ? g1 : ((w <= L.d2) ? g2 : g3);
+    return (w > L.d0 && w < L.d3) ? g : 0.f;
 }
 
 __device__ __forceinline__ float lin_G(const Lin &L, float w) {
-    if (!(w > L.d0)) return 0.f;
-    if (!(w < L.d3)) return 1.f;
-    if (w <= L.d1) {
-        const float x = w - L.d0;
-        return L.k1 * (1.f / 3.f) * x * x * x;
-    }
-    if (w <= L.d2) {
-        const float x = w - L.d1, d21 = L.d1 - L.d0;
-        return L.g2c * (d21 * d21 + x * (3.f * d21 + x * (3.f - L.k2b * x)));
-    }
-    const float y = L.d3 - w;
-    return 1.f - L.k3 * (1.f / 3.f) * y * y * y;
+    const float x1 = w - L.d0, x2 = w - L.d1, y = L.d3 - w, d21 = L.d1 - L.d0;
+    const float G1 = L.k1 * (1.f / 3.f) * x1 * x1 * x1;
+    const float G2 = L.g2c * (d21 * d21 + x2 * (3.f * d21 + x2 * (3.f - L.k2b * x2)));
+    const float G3 = 1.f - L.k3 * (1.f / 3.f) * y * y * y;
+    const float G = (w <= L.d1) ? G1 : ((w <= L.d2) ? G2 : G3);
+    return !(w > L.d0) ? 0.f : (!(w < L.d3) ? 1.f : G);
 }
 
 // Mean spacing of the energy grid (or bin width), the scale of the
@@ -136,29 +148,75 @@ __device__ __forceinline__ float hash_dither(uint32_t key) {
     return (float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f;
 }
 
-// First index i in [0, n) with om[i] > x (or n).
-__device__ __forceinline__ int upper_index(const float *om, int n, float x) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (om[mid] > x) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
+// First index i in [0, n) with om[i] > x (or n), from the index a uniform
+// grid would give (om0 + i / inv_de), corrected against the grid itself, so
+// any ascending grid gives the exact index.
+__device__ __forceinline__ int upper_index(const float *om, int n, float x, float om0, float inv_de) {
+    const float e = fminf(fmaxf((x - om0) * inv_de, -1.f), (float)n + 1.f);
+    int i = min(max((int)ceilf(e), 0), n);
+    while (i > 0 && om[i - 1] > x) --i;
+    while (i < n && !(om[i] > x)) ++i;
+    return i;
 }
 
-// First index i in [0, n) with om[i] >= x (or n).
-__device__ __forceinline__ int lower_index(const float *om, int n, float x) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (om[mid] >= x) hi = mid;
-        else lo = mid + 1;
-    }
-    return lo;
+// First index i in [0, n) with om[i] >= x (or n), as upper_index.
+__device__ __forceinline__ int lower_index(const float *om, int n, float x, float om0, float inv_de) {
+    const float e = fminf(fmaxf((x - om0) * inv_de, -1.f), (float)n + 1.f);
+    int i = min(max((int)ceilf(e), 0), n);
+    while (i > 0 && om[i - 1] >= x) --i;
+    while (i < n && !(om[i] >= x)) ++i;
+    return i;
 }
 
-// Adds sign * nu * (distribution of D) of one sub-tetrahedron to the tile.
+// Adds one sub-tetrahedron's distribution of D to the tile.
+__device__ void deposit(const SubTet &T, const SpecArgs &S) {
+    Lin L;
+    L.d0 = T.d0; L.d1 = T.d1; L.d2 = T.d2; L.d3 = T.d3;
+    const float d21 = T.d1 - T.d0, d31 = T.d2 - T.d0, d41 = T.d3 - T.d0;
+    const float d32 = T.d2 - T.d1, d42 = T.d3 - T.d1, d43 = T.d3 - T.d2;
+    L.k1 = d21 > 0.f ? 3.f / (d21 * d31 * d41) : 0.f;
+    L.k2a = (d31 > 0.f) ? 3.f / (d31 * d41) : 0.f;
+    L.k2b = (d32 > 0.f && d42 > 0.f) ? (d31 + d42) / (d32 * d42) : 0.f;
+    L.k3 = d43 > 0.f ? 3.f / (d41 * d42 * d43) : 0.f;
+    L.g2c = (d31 > 0.f) ? 1.f / (d31 * d41) : 0.f;
+    int i0, i1;   // indices [i0, i1)
+    if (S.mode == TETRA_BIN) {
+        i0 = max(0, upper_index(S.om, S.n_om + 1, T.d0, S.om0, S.inv_de) - 1);   // bins with upper edge > d0
+        i1 = min(S.n_om, upper_index(S.om, S.n_om + 1, T.d3, S.om0, S.inv_de));   // and lower edge <= d3
+    } else {
+        i0 = upper_index(S.om, S.n_om, T.d0, S.om0, S.inv_de);
+        i1 = lower_index(S.om, S.n_om, T.d3, S.om0, S.inv_de);
+    }
+    const float dith = hash_dither(T.key);
+    float Gp = (S.mode == TETRA_BIN && i0 < i1) ? lin_G(L, S.om[i0]) : 0.f;
+    for (int i = i0; i < i1; ++i) {
+        float v;
+        if (S.mode == TETRA_BIN) {
+            const float Gn = lin_G(L, S.om[i + 1]);
+            v = (Gn - Gp) / (S.om[i + 1] - S.om[i]);
+            Gp = Gn;
+        } else {
+            v = lin_g(L, S.om[i]);
+        }
+        const float x = fmaf(T.amp, v, dith);
+        long long qv;
+        if (fabsf(x) < 4194304.f) {
+            // round to nearest even by adding 1.5 * 2^23 (exact below 2^22):
+            // the same integer as the 64-bit conversion, without the FP64
+            // pipe that conversion runs on
+            qv = __float_as_int(x + 12582912.f) - 0x4B400000;
+        } else if (fabsf(x) < 4.0e18f) {
+            qv = __float2ll_rn(x);
+        } else {
+            atomicOr(S.status, kFlagRange);
+            qv = 0;
+        }
+        if (qv) atomicAdd(reinterpret_cast<unsigned long long *>(&S.tile[i]), static_cast<unsigned long long>(qv));
+    }
+}
+
+// Queues sign * nu * (distribution of D) of one sub-tetrahedron in this
+// warp's queue (or adds it at once when the queue is full).
 __device__ __noinline__ void accumulate(P5 v0, P5 v1, P5 v2, P5 v3, float sign, uint32_t key,
                                         const SpecArgs S) {
     const float u00 = v0.l0 - v3.l0, u01 = v0.l1 - v3.l1, u02 = v0.l2 - v3.l2;
@@ -174,43 +232,23 @@ __device__ __noinline__ void accumulate(P5 v0, P5 v1, P5 v2, P5 v3, float sign, 
     // a flat transition energy is a delta: measure zero in point mode, its
     // whole weight in the bin that holds it in bin mode
     if (S.mode != TETRA_BIN && !(d[3] > d[0])) return;
-    Lin L;
-    L.d0 = d[0]; L.d1 = d[1]; L.d2 = d[2]; L.d3 = d[3];
-    const float d21 = d[1] - d[0], d31 = d[2] - d[0], d41 = d[3] - d[0];
-    const float d32 = d[2] - d[1], d42 = d[3] - d[1], d43 = d[3] - d[2];
-    L.k1 = d21 > 0.f ? 3.f / (d21 * d31 * d41) : 0.f;
-    L.k2a = (d31 > 0.f) ? 3.f / (d31 * d41) : 0.f;
-    L.k2b = (d32 > 0.f && d42 > 0.f) ? (d31 + d42) / (d32 * d42) : 0.f;
-    L.k3 = d43 > 0.f ? 3.f / (d41 * d42 * d43) : 0.f;
-    L.g2c = (d31 > 0.f) ? 1.f / (d31 * d41) : 0.f;
-    const float amp = sign * nu * S.scale;
-    int i0, i1;   // indices [i0, i1)
-    if (S.mode == TETRA_BIN) {
-        i0 = max(0, upper_index(S.om, S.n_om + 1, d[0]) - 1);   // bins with upper edge > d0
-        i1 = min(S.n_om, upper_index(S.om, S.n_om + 1, d[3]));   // and lower edge <= d3
-    } else {
-        i0 = upper_index(S.om, S.n_om, d[0]);
-        i1 = lower_index(S.om, S.n_om, d[3]);
-    }
-    const float dith = hash_dither(key);
-    float Gp = (S.mode == TETRA_BIN && i0 < i1) ? lin_G(L, S.om[i0]) : 0.f;
-    for (int i = i0; i < i1; ++i) {
-        float v;
-        if (S.mode == TETRA_BIN) {
-            const float Gn = lin_G(L, S.om[i + 1]);
-            v = (Gn - Gp) / (S.om[i + 1] - S.om[i]);
-            Gp = Gn;
-        } else {
-            v = lin_g(L, S.om[i]);
-        }
-        const float x = fmaf(amp, v, dith);
-        if (fabsf(x) < 4.0e18f) {
-            const long long qv = __float2ll_rn(x);
-            if (qv) atomicAdd(reinterpret_cast<unsigned long long *>(&S.tile[i]), static_cast<unsigned long long>(qv));
-        } else {
-            atomicOr(S.status, kFlagRange);
-        }
-    }
+    // no grid energy (bin) in reach
+    if (d[3] < S.om[0] || d[0] > S.om_last) return;
+    const SubTet T{d[0], d[1], d[2], d[3], sign * nu * S.scale, key};
+    const int slot = atomicAdd(S.qn, 1);
+    if (slot < kQueueCap) S.q[slot] = T;
+    else deposit(T, S);
+}
+
+// Every lane of the warp takes queued sub-tetrahedra in turn; the queue is
+// empty afterwards. Called by all 32 lanes together.
+__device__ __forceinline__ void drain(const SpecArgs &S, int lane) {
+    __syncwarp();
+    const int n = min(*S.qn, kQueueCap);
+    for (int e = lane; e < n; e += 32) deposit(S.q[e], S);
+    __syncwarp();
+    if (lane == 0) *S.qn = 0;
+    __syncwarp();
 }
 
 // Cuts tetrahedron (v0..v3) to {field(which) < 0} and accumulates the kept
@@ -274,98 +312,119 @@ __device__ __noinline__ void region(P5 v0, P5 v1, P5 v2, P5 v3, int first, int s
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kSpecThreads)
+__global__ void __launch_bounds__(kSpecThreads, kSpecBlocksPerSM)
     spectral_t0_kernel(const float *eps, int eps_stride, int n1, int n2, int n3, int nx, int ny, int z0, int z1,
                        int qx, int qy, int qz, float mu, const float *omega, int n_om, int mode,
                        long long *partials, int *status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    long long *tile = reinterpret_cast<long long *>(smem);
+    SubTet *queues = reinterpret_cast<SubTet *>(smem);                         // [warps][kQueueCap]
+    int *qcount = reinterpret_cast<int *>(queues + kSpecWarps * kQueueCap);    // [warps]
+    long long *tile = reinterpret_cast<long long *>(qcount + 2 * kSpecWarps); // 8-byte aligned
     float *om = reinterpret_cast<float *>(tile + n_om);
     const int n_edges = (mode == TETRA_BIN) ? n_om + 1 : n_om;
     for (int i = threadIdx.x; i < n_om; i += blockDim.x) tile[i] = 0;
     for (int i = threadIdx.x; i < n_edges; i += blockDim.x) om[i] = omega[i];
+    if (threadIdx.x < kSpecWarps) qcount[threadIdx.x] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // V_T/V_G in fixed-point units: de * 2^26
-    const float scale = (float)ldexp(mean_spacing(om, n_om, mode), kSpecBits);
-    const SpecArgs S{om, tile, n_om, mode, scale, status};
+    const double de = mean_spacing(om, n_om, mode);
+    const float scale = (float)ldexp(de, kSpecBits);
+    const float om_lo = om[0], om_hi = om[n_edges - 1];
+    const SpecArgs S{om, tile, n_om, mode, scale, status, om_lo, om_hi, (float)(1.0 / de),
+                     queues + warp * kQueueCap, qcount + warp};
     // energy range of the grid: a band pair whose transition energies over a
     // tetrahedron miss it contributes nothing (the clipped regions' values
     // lie between the corner minimum and maximum); the +1 region has positive
     // transition energies, the -1 region negative ones
-    const float om_lo = om[0], om_hi = om[n_edges - 1];
     const long n_items = 6L * n1 * n2 * (long)(z1 - z0);
-    for (long it = blockIdx.x * (long)blockDim.x + threadIdx.x; it < n_items; it += (long)gridDim.x * blockDim.x) {
-        const int t = (int)(it % 6);
-        const long cube = it / 6;
-        const int x = (int)(cube % n1), y = (int)((cube / n1) % n2), z = z0 + (int)(cube / ((long)n1 * n2));
-        float a[4][NB], c[4][NB];
+    const long stride = (long)gridDim.x * blockDim.x;
+    // whole warps step through the items together (the queue is drained by
+    // all 32 lanes); a lane past the end takes part without items
+    for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_items; base += stride) {
+        const long it = base + lane;
+        const bool valid = it < n_items;
+        float a[4][NB], c[4][NB];   // indexed by band at run time below
+        if (valid) {
+            const int t = (int)(it % 6);
+            const long cube = it / 6;
+            const int x = (int)(cube % n1), y = (int)((cube / n1) % n2), z = z0 + (int)(cube / ((long)n1 * n2));
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int cl = kSpecTable[t][v];
-            const int xx = x + (cl & 1), yy = y + ((cl >> 1) & 1), zz = z + (cl >> 2);
-            // the point itself: the layout's halo covers xx = n1 etc.
-            const long p = xx + (long)nx * (yy + (long)ny * zz);
-            // the point shifted by q, reduced into the grid
-            // (xx <= n1 and 0 <= qx < n1, so one subtraction reduces it)
-            int sx = xx + qx, sy = yy + qy, sz = zz + qz;
-            sx -= (sx >= n1) ? n1 : 0;
-            sy -= (sy >= n2) ? n2 : 0;
-            sz -= (sz >= n3) ? n3 : 0;
-            const long pq = sx + (long)nx * (sy + (long)ny * sz);
+            for (int v = 0; v < 4; ++v) {
+                const int cl = kSpecTable[t][v];
+                const int xx = x + (cl & 1), yy = y + ((cl >> 1) & 1), zz = z + (cl >> 2);
+                // the point itself: the layout's halo covers xx = n1 etc.
+                const long p = xx + (long)nx * (yy + (long)ny * zz);
+                // the point shifted by q, reduced into the grid
+                // (xx <= n1 and 0 <= qx < n1, so one subtraction reduces it)
+                int sx = xx + qx, sy = yy + qy, sz = zz + qz;
+                sx -= (sx >= n1) ? n1 : 0;
+                sy -= (sy >= n2) ? n2 : 0;
+                sz -= (sz >= n3) ? n3 : 0;
+                const long pq = sx + (long)nx * (sy + (long)ny * sz);
 #pragma unroll
-            for (int n = 0; n < NB; ++n) {
-                a[v][n] = eps[p * eps_stride + n] - mu;
-                c[v][n] = eps[pq * eps_stride + n] - mu;
+                for (int n = 0; n < NB; ++n) {
+                    a[v][n] = eps[p * eps_stride + n] - mu;
+                    c[v][n] = eps[pq * eps_stride + n] - mu;
+                }
             }
         }
         // per band: some corner occupied (an), some corner empty (ap); the
         // same for the bands at k + q (cn: occupied, cp: empty)
         uint32_t an = 0, ap = 0, cn = 0, cp = 0, a_all = 0, c_all = 0;
+        if (valid) {
 #pragma unroll
-        for (int n = 0; n < NB; ++n) {
-            const float amin = fminf(fminf(a[0][n], a[1][n]), fminf(a[2][n], a[3][n]));
-            const float amax = fmaxf(fmaxf(a[0][n], a[1][n]), fmaxf(a[2][n], a[3][n]));
-            const float cmin = fminf(fminf(c[0][n], c[1][n]), fminf(c[2][n], c[3][n]));
-            const float cmax = fmaxf(fmaxf(c[0][n], c[1][n]), fmaxf(c[2][n], c[3][n]));
-            an |= (amin < 0.f ? 1u : 0u) << n;
-            ap |= (amax > 0.f ? 1u : 0u) << n;
-            cn |= (cmin < 0.f ? 1u : 0u) << n;
-            cp |= (cmax > 0.f ? 1u : 0u) << n;
-            a_all |= (amax < 0.f ? 1u : 0u) << n;   // occupied at every corner
-            c_all |= (cmin > 0.f ? 1u : 0u) << n;   // empty at every corner
-        }
-#pragma unroll
-        for (int n = 0; n < NB; ++n) {
-#pragma unroll
-            for (int m = 0; m < NB; ++m) {
-                bool plus = ((an >> n) & 1u) && ((cp >> m) & 1u);
-                bool minus = ((ap >> n) & 1u) && ((cn >> m) & 1u);
-                if (!plus && !minus) continue;
-                const float d0 = c[0][m] - a[0][n], d1 = c[1][m] - a[1][n];
-                const float d2 = c[2][m] - a[2][n], d3 = c[3][m] - a[3][n];
-                const float dlo = fminf(fminf(d0, d1), fminf(d2, d3)), dhi = fmaxf(fmaxf(d0, d1), fmaxf(d2, d3));
-                if (dhi < om_lo || dlo > om_hi) continue;
-                plus = plus && om_hi > 0.f;
-                minus = minus && om_lo < 0.f;
-                if (!plus && !minus) continue;
-                const P5 v0{1.f, 0.f, 0.f, a[0][n], c[0][m]};
-                const P5 v1{0.f, 1.f, 0.f, a[1][n], c[1][m]};
-                const P5 v2{0.f, 0.f, 1.f, a[2][n], c[2][m]};
-                const P5 v3{0.f, 0.f, 0.f, a[3][n], c[3][m]};
-                const uint32_t key = ((uint32_t)it * (uint32_t)(NB * NB) + (uint32_t)(n * NB + m)) * 2u;
-                // band n occupied and band m empty at every corner: the +1
-                // region is the whole tetrahedron (the same sub-tetrahedron and
-                // dither key the two cuts would produce)
-                if (((a_all >> n) & 1u) && ((c_all >> m) & 1u)) {
-                    accumulate(v0, v1, v2, v3, 1.f, key * 16u, S);
-                    continue;
-                }
-                // +1 on {a < 0, c > 0}; -1 on {a > 0, c < 0}
-                if (plus) region(v0, v1, v2, v3, 0, 3, 1.f, key, S);
-                if (minus) region(v0, v1, v2, v3, 1, 2, -1.f, key + 1u, S);
+            for (int n = 0; n < NB; ++n) {
+                const float amin = fminf(fminf(a[0][n], a[1][n]), fminf(a[2][n], a[3][n]));
+                const float amax = fmaxf(fmaxf(a[0][n], a[1][n]), fmaxf(a[2][n], a[3][n]));
+                const float cmin = fminf(fminf(c[0][n], c[1][n]), fminf(c[2][n], c[3][n]));
+                const float cmax = fmaxf(fmaxf(c[0][n], c[1][n]), fmaxf(c[2][n], c[3][n]));
+                an |= (amin < 0.f ? 1u : 0u) << n;
+                ap |= (amax > 0.f ? 1u : 0u) << n;
+                cn |= (cmin < 0.f ? 1u : 0u) << n;
+                cp |= (cmax > 0.f ? 1u : 0u) << n;
+                a_all |= (amax < 0.f ? 1u : 0u) << n;   // occupied at every corner
+                c_all |= (cmin > 0.f ? 1u : 0u) << n;   // empty at every corner
             }
         }
+        // band pairs in a loop that is not unrolled (one copy of the code);
+        // the queue is drained between pairs once it holds kDrainAt entries
+#pragma unroll 1
+        for (int pr = 0; pr < NB * NB; ++pr) {
+            // lane 0's count, read after every push of the previous pair and
+            // before any of this one: the same decision in every lane
+            __syncwarp();
+            const int queued = __shfl_sync(0xffffffffu, *S.qn, 0);
+            if (queued >= kDrainAt) drain(S, lane);
+            const int n = pr / NB, m = pr - (pr / NB) * NB;
+            bool plus = ((an >> n) & 1u) && ((cp >> m) & 1u);
+            bool minus = ((ap >> n) & 1u) && ((cn >> m) & 1u);
+            if (!plus && !minus) continue;
+            const float d0 = c[0][m] - a[0][n], d1 = c[1][m] - a[1][n];
+            const float d2 = c[2][m] - a[2][n], d3 = c[3][m] - a[3][n];
+            const float dlo = fminf(fminf(d0, d1), fminf(d2, d3)), dhi = fmaxf(fmaxf(d0, d1), fmaxf(d2, d3));
+            if (dhi < om_lo || dlo > om_hi) continue;
+            plus = plus && om_hi > 0.f;
+            minus = minus && om_lo < 0.f;
+            if (!plus && !minus) continue;
+            const P5 v0{1.f, 0.f, 0.f, a[0][n], c[0][m]};
+            const P5 v1{0.f, 1.f, 0.f, a[1][n], c[1][m]};
+            const P5 v2{0.f, 0.f, 1.f, a[2][n], c[2][m]};
+            const P5 v3{0.f, 0.f, 0.f, a[3][n], c[3][m]};
+            const uint32_t key = ((uint32_t)it * (uint32_t)(NB * NB) + (uint32_t)(n * NB + m)) * 2u;
+            // band n occupied and band m empty at every corner: the +1
+            // region is the whole tetrahedron (the same sub-tetrahedron and
+            // dither key the two cuts would produce)
+            if (((a_all >> n) & 1u) && ((c_all >> m) & 1u)) {
+                accumulate(v0, v1, v2, v3, 1.f, key * 16u, S);
+                continue;
+            }
+            // +1 on {a < 0, c > 0}; -1 on {a > 0, c < 0}
+            if (plus) region(v0, v1, v2, v3, 0, 3, 1.f, key, S);
+            if (minus) region(v0, v1, v2, v3, 1, 2, -1.f, key + 1u, S);
+        }
     }
+    drain(S, lane);
     __syncthreads();
     long long *dst = partials + (long)blockIdx.x * n_om;
     for (int i = threadIdx.x; i < n_om; i += blockDim.x) dst[i] = tile[i];
@@ -382,11 +441,12 @@ __global__ void spectral_reduce_kernel(const long long *partials, int grid, int 
     }
 }
 
-// one CTA per SM: the kernel holds about 200 registers per thread
-int spectral_grid(const Plan &P) { return P.sm_count; }
+// persistent blocks, as many as fit an SM at the register bound
+int spectral_grid(const Plan &P) { return kSpecBlocksPerSM * P.sm_count; }
 
 size_t spectral_smem(int n_om, int mode) {
-    return sizeof(long long) * (size_t)n_om + sizeof(float) * (size_t)(mode == TETRA_BIN ? n_om + 1 : n_om);
+    return sizeof(SubTet) * kSpecWarps * kQueueCap + sizeof(int) * 2 * kSpecWarps + sizeof(long long) * (size_t)n_om +
+           sizeof(float) * (size_t)(mode == TETRA_BIN ? n_om + 1 : n_om);
 }
 
 template <int NB>
