@@ -218,6 +218,19 @@ def eig_ops_per_point(n_orb=8, n_R=7):
     return h_build + tridiag + qr + back + 2 * n * n
 
 
+def eig_bwd_ops_per_point(n_orb=8, n_R=7):
+    """Algorithmic FP32 FMA-pipe operations per k-point of the eigensolver
+    adjoint: the forward's eigensolver with its eigenvectors (recomputed;
+    eig_ops_per_point without the squared moduli), the pair sums of S
+    (n(n-1)/2 pairs x n orbitals: a weight difference, two complex products,
+    two accumulations), Y = S V^T (n^2 complex dot products of length n),
+    the Hermitian half of Z = conj(V) Y, and the phase sums (4 per complex
+    output (R, i, j), plus the diagonal)."""
+    n = n_orb
+    return (eig_ops_per_point(n, n_R) - 2 * n * n + 6 * n * n * (n - 1) // 2 + 4 * n ** 3 + 2 * n * n * (n + 1)
+            + 4 * n_R * n * n + n)
+
+
 def eig_roofline(torch, dev, points, ms):
     """The eigensolver's algorithmic FP32 throughput against the same FP32 peak."""
     mp = {}
@@ -360,9 +373,37 @@ def differentiation_workload(torch, T, steps, warmup, local):
     b.record(s_)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
+    # the two adjoints alone, on the step's eigen-data and seeded gradients
+    eps, w = plan.eig(params.detach(), R0)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    gd = torch.randn((8, nbins), device=dev, generator=gen)
+    ge = torch.randn(eps.shape, device=dev, generator=gen)
+    gw = torch.randn(w.shape, device=dev, generator=gen)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a.record(s_)
+        for _ in range(steps):
+            fn()
+        b.record(s_)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    dos_bwd_ms = timed(lambda: plan.dos_backward(eps, w, edges, gd))
+    eig_bwd_ms = timed(lambda: plan.eig_backward(params.detach(), R0, ge, gw))
+    roof = eig_roofline(torch, dev, n ** 3, eig_bwd_ms)
+    ops = eig_bwd_ops_per_point()
+    roof.update({"kernel": "tetra_eig_bwd_kernel", "achieved": 2.0 * ops * n ** 3 / (eig_bwd_ms * 1e-3) / 1e12,
+                 "algorithmic": f"{ops} FMA-pipe ops per k-point x {n ** 3} k-points (eigensolver with "
+                                "eigenvectors recomputed, pair sums of S, S V^T, Hermitian half of conj(V) S V^T, "
+                                "phase sums)"})
+    roof["frac"] = roof["achieved"] / roof["peak"]
     return {"workload": "8-orbital model, 64^3 grid, 200 bins, loss = sum (bin DOS - target)^2, "
                         "forward + backward to 904 model parameters (eig, bin DOS, both adjoints)",
-            "ms_per_step": ms, "grad_norm": float(params.grad.norm())}
+            "ms_per_step": ms, "grad_norm": float(params.grad.norm()),
+            "dos_backward_ms": dos_bwd_ms, "eig_backward_ms": eig_bwd_ms, "eig_backward_roofline": roof}
 
 
 def batched_workload(torch, T, mode, steps, warmup, local, count_window=True):

@@ -20,6 +20,9 @@ Pieces and the passages they follow (arXiv:1710.10789):
     with Fermi-Dirac occupations interpolated linearly (pair bands fed to
     ``dos``), and at T = 0 with step occupations clipped exactly inside each
     tetrahedron (C code).
+  * ``chi0_real_t0`` / ``t0_inverse_average``: the real part at T = 0 on the
+    same clipped sub-tetrahedra, the principal-value average of 1/(w - D)
+    over each (C code).
 
 Every numerical convention (grid, corner labels, region boundaries, the
 corrected dw3/dE term) is listed in the header of ``tetra_oracle.c``.
@@ -79,6 +82,8 @@ def _load():
             lib.oracle_t0_spectral.argtypes = [i, i, i, i, d, d, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
                                                i, i, d, d, i, i, d, i]
             lib.oracle_t0_spectral.restype = i
+            lib.oracle_t0_inverse_average.argtypes = [d, ctypes.c_double]
+            lib.oracle_t0_inverse_average.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -334,9 +339,9 @@ def pair_bands(eps, n1, n2, n3, q, kT, mu):
 
 # ---------------------------------------------------------------- spectral function at T = 0
 def _edges_pair(energies, mode, edges_hi):
-    if mode == "point":
+    if mode in ("point", "real"):
         ea = _c64(energies)
-        return ea, ea, 0
+        return ea, ea, 0 if mode == "point" else 2
     if edges_hi is None:
         e = _c64(energies)
         return np.ascontiguousarray(e[:-1]), np.ascontiguousarray(e[1:]), 1
@@ -347,12 +352,34 @@ def spectral_t0_tetra(a, c, energies, mode="point", edges_hi=None) -> np.ndarray
     """One tetrahedron's T = 0 spectral contribution in units of V_T/V_G:
     a[4] = e_n - mu and c[4] = e_m(k+q) - mu at its corners; the transition
     energy c - a over {a < 0, c > 0} counts +1, over {a > 0, c < 0} -1
-    (point density at ``energies``, or bin averages as in ``dos``)."""
+    (point density at ``energies``, or bin averages as in ``dos``; mode
+    "real": the principal-value average of 1/(w - D) instead, the real part
+    of chi0)."""
     lib = _load()
     ea, eb, m = _edges_pair(energies, mode, edges_hi)
     out = np.zeros(ea.shape[0])
     lib.oracle_t0_tetra(_p(_c64(a)), _p(_c64(c)), m, ea.shape[0], _p(ea), _p(eb), _p(out))
     return out
+
+
+def t0_inverse_average(d, w) -> float:
+    """Principal-value average of 1/(w - D) over a tetrahedron on whose
+    corners the linear function D takes the values d[4] (C code: the
+    density's three quadratic pieces integrated against 1/(w - x) in closed
+    form near w and by their moment series far from it)."""
+    lib = _load()
+    return float(lib.oracle_t0_inverse_average(_p(_c64(d)), float(w)))
+
+
+def chi0_real_t0(eps, n1, n2, n3, q, mu, energies, eps_kq=None, z_range=None, nthreads: int = 1) -> np.ndarray:
+    """Real part of the T = 0 bare susceptibility at the points ``energies``,
+    Re chi0(q, w) = sum_{n,m} (1/V_G) P int [Theta(mu - e_n(k)) - Theta(mu - e_m(k+q))]
+                    / (w - e_m(k+q) + e_n(k)) dk,
+    the Hilbert transform of ``spectral_t0``: the same exact clipping, each
+    sub-tetrahedron adding sign * nu * P<1/(w - D)> (``t0_inverse_average``).
+    Arguments as ``spectral_t0``. Returns (npts,)."""
+    return spectral_t0(eps, n1, n2, n3, q, mu, energies, mode="real", eps_kq=eps_kq, z_range=z_range,
+                       nthreads=nthreads)
 
 
 def spectral_t0(eps, n1, n2, n3, q, mu, energies, mode="point", edges_hi=None, eps_kq=None,

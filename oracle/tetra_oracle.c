@@ -515,12 +515,99 @@ static void t0_density(const double d_in[4], double w, double *g, double *G) {
     }
 }
 
+/* ---- real part: principal-value average of 1/(w - D) over a tetrahedron --
+ *
+ * Re chi0(q, w) = sum_{n,m} (1/V_G) P int dk [f_n(k) - f_m(k+q)] / (w - D(k)),
+ * D = e_m(k+q) - e_n(k), the Hilbert transform of S (chi0 = int S(w') /
+ * (w - w' + i0) dw'). Over a sub-tetrahedron the average of 1/(w - D) is the
+ * principal-value integral of the normalised density g of D against
+ * 1/(w - x). g is a quadratic spline on the sorted corner values
+ * d0 <= d1 <= d2 <= d3 (the density of t0_density); on its three pieces its
+ * Bernstein coefficients are
+ *   [d0, d1]: (0, 0, G1),  [d1, d2]: (G1, 3/d41, G2),  [d2, d3]: (G2, 0, 0),
+ * G1 = 3 d21 / (d31 d41) = g(d1), G2 = 3 d43 / (d41 d42) = g(d2) (the middle
+ * coefficient follows from g's slope at d1 or d2; all three pieces integrate
+ * to d21 G1/3 + d32 (G1 + 3/d41 + G2)/3 + d43 G2/3 = 1).
+ *
+ * A piece [a, b], h = b - a, with coefficients (b0, b1, b2), p(t) = b0 (1-t)^2 +
+ * 2 b1 t (1-t) + b2 t^2, gives int_0^1 p(t) / (s - t) dt with s = (w - a)/h:
+ *  - far from the piece (|s - 1/2| >= 3/2) as the series
+ *    sum_j m_j / (s - 1/2)^(j+1), m_j = int_0^1 p(t) (t - 1/2)^j dt, whose
+ *    terms shrink by 1/3 or more (no cancellation, however thin the piece);
+ *  - near it in closed form, with I0 = ln|s| - ln|s - 1| (the principal
+ *    value inside the piece), int t/(s-t) = s I0 - 1, int t^2/(s-t) =
+ *    s^2 I0 - s - 1/2:
+ *      p(s) I0 + b0 (3/2 - s) + b1 (2s - 1) - b2 (s + 1/2),
+ *    p(s) the piece's polynomial continued to t = s.
+ * When w is exactly a knot the two pieces that meet there both drop their
+ * ln|w - knot| term: its coefficients are g's values from both sides, equal
+ * since g is continuous, so the terms cancel and only ln h remains.
+ */
+static double t0_piece_inverse(double b0, double b1, double b2, double a, double b, double w) {
+    const double h = b - a, s = (w - a) / h, u = s - 0.5;
+    if (fabs(u) >= 1.5) {
+        /* p(t) = A + B tau + C tau^2 with tau = t - 1/2; the moments of tau
+         * over [-1/2, 1/2] vanish for odd powers and are 2^-k/(k+1) for even k */
+        const double A = 0.25 * (b0 + 2.0 * b1 + b2), B = b2 - b0, C = b0 - 2.0 * b1 + b2;
+        double sum = 0.0, upow = 1.0 / u;
+        int j;
+        for (j = 0; j <= 60; ++j) {
+            double mj = 0.0;
+            int k;
+            for (k = j; k <= j + 2; ++k) {
+                const double coef = (k == j) ? A : ((k == j + 1) ? B : C);
+                if (k % 2 == 0) mj += coef * ldexp(1.0, -k) / (double)(k + 1);
+            }
+            sum += mj * upow;
+            upow /= u;
+        }
+        return sum;
+    }
+    {
+        /* ln|s| = ln|w - a| - ln h and ln|s - 1| = ln|w - b| - ln h, taken from
+         * the distances themselves (no cancellation near a knot) */
+        const double lh = log(h);
+        const double la = ((w == a) ? 0.0 : log(fabs(w - a))) - lh;
+        const double lb = ((w == b) ? 0.0 : log(fabs(w - b))) - lh;
+        const double ps = b0 * (1.0 - s) * (1.0 - s) + 2.0 * b1 * s * (1.0 - s) + b2 * s * s;
+        return ps * (la - lb) + b0 * (1.5 - s) + b1 * (2.0 * s - 1.0) - b2 * (s + 0.5);
+    }
+}
+
+/* P <1/(w - D)> over a tetrahedron on whose corners the linear function D
+ * takes the values d_in[4] (uniform measure). A flat D (all values equal)
+ * gives 1/(w - d), and 0 when w equals it. */
+double oracle_t0_inverse_average(const double d_in[4], double w) {
+    double d[4];
+    int i, j;
+    for (i = 0; i < 4; ++i) d[i] = d_in[i];
+    for (i = 1; i < 4; ++i) {
+        const double v = d[i];
+        j = i - 1;
+        while (j >= 0 && d[j] > v) { d[j + 1] = d[j]; --j; }
+        d[j + 1] = v;
+    }
+    if (!(d[3] > d[0])) return (w == d[0]) ? 0.0 : 1.0 / (w - d[0]);
+    {
+        const double d21 = d[1] - d[0], d31 = d[2] - d[0], d41 = d[3] - d[0];
+        const double d32 = d[2] - d[1], d42 = d[3] - d[1], d43 = d[3] - d[2];
+        const double G1 = d31 > 0.0 ? 3.0 * d21 / (d31 * d41) : 0.0;
+        const double G2 = d42 > 0.0 ? 3.0 * d43 / (d41 * d42) : 0.0;
+        double r = 0.0;
+        if (d21 > 0.0) r += t0_piece_inverse(0.0, 0.0, G1, d[0], d[1], w);
+        if (d32 > 0.0) r += t0_piece_inverse(G1, 3.0 / d41, G2, d[1], d[2], w);
+        if (d43 > 0.0) r += t0_piece_inverse(G2, 0.0, 0.0, d[2], d[3], w);
+        return r;
+    }
+}
+
 /*
  * Contribution of one tetrahedron (vertex values a[4] = e_n - mu,
  * c[4] = e_m(k+q) - mu) to the normalised spectral function, in units of
  * V_T / V_G: mode 0 (point) sum_regions sign * nu * g(ea[i]); mode 1 (bin)
- * sum_regions sign * nu * [G(eb[i]) - G(ea[i])] / (eb[i] - ea[i]). Adds to
- * out[i], i < npts.
+ * sum_regions sign * nu * [G(eb[i]) - G(ea[i])] / (eb[i] - ea[i]); mode 2
+ * (real part of chi0 at the points ea) sum_regions sign * nu *
+ * P<1/(ea[i] - D)>. Adds to out[i], i < npts.
  */
 void oracle_t0_tetra(const double a[4], const double c[4], int mode, int npts, const double *ea,
                      const double *eb, double *out) {
@@ -550,6 +637,10 @@ void oracle_t0_tetra(const double a[4], const double c[4], int mode, int npts, c
                 for (q = 0; q < 4; ++q) d[q] = B[ib][q].c - B[ib][q].a;
                 for (i = 0; i < npts; ++i) {
                     double g, G, gb, Gb;
+                    if (mode == 2) {
+                        out[i] += sign * nu * oracle_t0_inverse_average(d, ea[i]);
+                        continue;
+                    }
                     t0_density(d, ea[i], &g, &G);
                     if (mode == 0) {
                         out[i] += sign * nu * g;

@@ -729,3 +729,109 @@ def test_t0_spectral_grid_against_monte_carlo():
                             acc += h / ntet
                             var += (sg / ntet) ** 2
     assert np.all(np.abs(s - acc) <= 5 * np.sqrt(var) + 1e-4), np.max(np.abs(s - acc))
+
+
+# ---- real part of the T = 0 susceptibility --------------------------------
+
+def linear_density(d, x):
+    """Normalised density of a linear function with corner values d over a
+    tetrahedron, read from the oracle's T = 0 tetrahedron in a configuration
+    where the +1 region is the whole tetrahedron (a < 0 < c at every corner;
+    that density is pinned above by Monte-Carlo histograms)."""
+    a = -10.0 * np.ones(4)
+    c = np.asarray(d, float) + 100.0
+    return float(oracle.spectral_t0_tetra(a, c, np.atleast_1d(x) + 110.0)[0])
+
+
+def principal_value_by_quadrature(d, w):
+    """P int g(x) / (w - x) dx by adaptive quadrature (QUADPACK), split at the
+    corner values; the piece holding w with the Cauchy weight."""
+    from scipy import integrate
+    knots = sorted(set(float(v) for v in d))
+    tot = 0.0
+    for lo, hi in zip(knots[:-1], knots[1:]):
+        if lo < w < hi:
+            v, _ = integrate.quad(lambda x: linear_density(d, x), lo, hi, weight="cauchy", wvar=w,
+                                  limit=500, epsabs=1e-14, epsrel=1e-12)
+            tot -= v
+        else:
+            v, _ = integrate.quad(lambda x: linear_density(d, x) / (w - x), lo, hi, limit=500,
+                                  epsabs=1e-14, epsrel=1e-12)
+            tot += v
+    return tot
+
+
+@pytest.mark.parametrize("trial", range(12))
+def test_t0_inverse_average_against_quadrature(trial):
+    """P<1/(w - D)> over a tetrahedron (closed-form pieces near w, moment
+    series far from it) against adaptive quadrature of the density, for
+    energies inside each piece, near the knots, beside and far outside the
+    support, with nearly coincident and coincident corner values."""
+    rng = np.random.default_rng(100 + trial)
+    d = np.sort(rng.normal(0, 1, 4))
+    if trial % 4 == 1:
+        d[1] = d[0] + 1e-7
+    if trial % 4 == 2:
+        d[2] = d[1]
+    if trial % 4 == 3:
+        d[3] = d[2] + 1e-9
+    ws = list(rng.uniform(d[0] - 1, d[3] + 1, 3)) + [0.5 * (d[0] + d[3]), d[1] + 1e-3, d[2] - 1e-3,
+                                                       d[3] + 5.0, d[0] - 30.0]
+    for w in ws:
+        r = oracle.t0_inverse_average(d, w)
+        ref = principal_value_by_quadrature(d, w)
+        assert abs(r - ref) <= 1e-8 * abs(ref) + 1e-12, (d, w, r, ref)
+
+
+@pytest.mark.parametrize("w", [3.5, 6.0, -4.0])
+def test_t0_inverse_average_far_field_monte_carlo(w):
+    """Outside the range of D the integrand is smooth: the plain Monte-Carlo
+    mean of 1/(w - D) over uniform points of the tetrahedron."""
+    rng = np.random.default_rng(7)
+    d = rng.normal(0, 1, 4)
+    lam = rng.dirichlet(np.ones(4), 1_000_000)
+    vals = 1.0 / (w - lam @ d)
+    mc, se = vals.mean(), vals.std() / np.sqrt(len(vals))
+    assert abs(oracle.t0_inverse_average(d, w) - mc) < 5 * se
+
+
+def test_t0_inverse_average_flat_knots_and_continuity():
+    """A flat D gives 1/(w - d); at a corner value the result is finite and
+    equals the limit from both sides (the logarithms of the two pieces that
+    meet there cancel); corner order does not matter."""
+    assert oracle.t0_inverse_average([0.3] * 4, 1.3) == pytest.approx(1.0)
+    d = np.array([-0.7, 0.1, 0.35, 1.2])
+    for k in d:
+        r = oracle.t0_inverse_average(d, k)
+        side = 0.5 * (oracle.t0_inverse_average(d, k + 1e-9) + oracle.t0_inverse_average(d, k - 1e-9))
+        assert np.isfinite(r) and abs(r - side) < 1e-7
+    assert oracle.t0_inverse_average(d[::-1].copy(), 0.2) == pytest.approx(oracle.t0_inverse_average(d, 0.2),
+                                                                          rel=1e-14)
+
+
+def test_chi0_real_is_the_hilbert_transform_of_s():
+    """Kramers-Kronig on the grid: Re chi0(q, w) = P int S(q, w') / (w - w') dw',
+    with S from the oracle's exact bin averages on 6000 bins (the transform of
+    a piecewise-constant S is a sum of logarithms); agreement to the binning
+    error. Also Re chi0(-q, -w) = Re chi0(q, w) (S is odd under that map),
+    and Re chi0 -> M1 / w^2 for large w, M1 = int w' S(w') dw' (S has zero
+    total weight)."""
+    n = (5, 4, 4)
+    model = tbgen.tb_model(9, n_orb=3)
+    eps, _ = oracle.eig(model, *n)
+    mu = float(np.median(eps))
+    q = (2, 1, 0)
+    span = float(eps.max() - eps.min()) + 0.5
+    edges = np.linspace(-span, span, 6001)
+    s = oracle.spectral_t0(eps, *n, q, mu, edges, mode="bin")
+    w = np.array([-2.3, -0.6, 0.05, 0.9, 2.2, 4.5])
+    r = oracle.chi0_real_t0(eps, *n, q, mu, w)
+    lo, hi = edges[:-1], edges[1:]
+    kk = np.array([np.sum(s * np.log(np.abs((x - lo) / (x - hi)))) for x in w])
+    assert np.max(np.abs(r - kk)) < 2e-3 * np.max(np.abs(r)), (r, kk)
+    rm = oracle.chi0_real_t0(eps, *n, tuple(-v for v in q), mu, -w)
+    np.testing.assert_allclose(rm, r, rtol=0, atol=1e-12 * np.max(np.abs(r)))
+    big = np.array([400.0, 800.0])
+    m1 = float(np.sum(s * 0.5 * (lo + hi) * (hi - lo)))
+    rb = oracle.chi0_real_t0(eps, *n, q, mu, big)
+    np.testing.assert_allclose(rb * big ** 2, m1, rtol=2e-2)
