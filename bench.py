@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e and extra measurements")
     ap.add_argument("--variant", default=None,
-                    choices=["differentiation", "paper_shape", "lindhard", "spectral_t0", "near_balance"],
+                    choices=["differentiation", "paper_shape", "lindhard", "spectral_t0", "chi0_real_t0",
+                             "near_balance"],
                     help="run one extra workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -642,6 +643,38 @@ def spectral_t0_workload(torch, T, steps, warmup, local):
             "spectral_weight_0_to_4eV": float(out.sum()) * 4.0 / 399}
 
 
+def chi0_real_t0_workload(torch, T, steps, warmup, local):
+    """Real part of the T = 0 bare susceptibility (tetra_chi0_real_t0) on the
+    8-orbital model, 64^3 grid, q = (16, 0, 0), chemical potential at 4
+    electrons per spin, 400 energies on [0, 4] eV."""
+    import tbgen
+    dev = torch.device("cuda", local)
+    n = 64
+    p_np, R_np = model_arrays(tbgen.tb_model(0, n_orb=8))
+    plan = T.Plan(n, n, n, 8, 8, 16, device=local)
+    eps, w = plan.eig(torch.from_numpy(p_np).to(dev), torch.from_numpy(R_np).to(dev))
+    mu = plan.fermi_level(eps, w, 4.0)
+    omega = torch.from_numpy(tbgen.uniform_grid(0.0, 4.0, 400)).to(dev)
+    out = torch.empty((400,), dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        plan.chi0_real_t0(eps, (16, 0, 0), mu, omega, out=out)
+    torch.cuda.synchronize()
+    s_ = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(s_)
+    for _ in range(steps):
+        plan.chi0_real_t0(eps, (16, 0, 0), mu, omega, out=out)
+    b.record(s_)
+    torch.cuda.synchronize()
+    assert plan.spectral_status() == T.TETRA_OK
+    return {"workload": "real part of the bare susceptibility Re chi0(q, w) at T = 0 (exact double-band "
+                        "clipping, principal-value averages), 8-orbital model, 64^3 grid, q = (16, 0, 0), "
+                        "64 band pairs, 400 energies on [0, 4] eV",
+            "ms_per_evaluation": a.elapsed_time(b) / steps, "chemical_potential_eV": mu,
+            "re_chi0_at_0_eV": float(out[0]), "re_chi0_at_4_eV": float(out[-1])}
+
+
 def cpu_baseline(n, n_omega, seed=0, planes=None, threads=None, stride=1, omega=None, keep=False):
     """The FP64 oracle on the host cores over a bounded sample of the same
     workload: `planes` cube planes (n x n x planes cubes) of the n^3 grid, all
@@ -785,7 +818,8 @@ def main():
                                       torch.from_numpy(R_np).to(dev), args.steps, args.warmup, local)
         else:
             fn = {"differentiation": differentiation_workload, "paper_shape": paper_shape_workload,
-                  "lindhard": lindhard_workload, "spectral_t0": spectral_t0_workload}[args.variant]
+                  "lindhard": lindhard_workload, "spectral_t0": spectral_t0_workload,
+                  "chi0_real_t0": chi0_real_t0_workload}[args.variant]
             r = fn(torch, T, args.steps, args.warmup, local)
         if rank == 0:
             print(json.dumps(r), flush=True)
@@ -907,6 +941,7 @@ def main():
             variants["integrated"] = integrated_workload(torch, T, n, eps, w, args.steps, args.warmup, local)
         variants["lindhard"] = lindhard_workload(torch, T, args.steps, args.warmup, local)
         variants["spectral_t0"] = spectral_t0_workload(torch, T, args.steps, args.warmup, local)
+        variants["chi0_real_t0"] = chi0_real_t0_workload(torch, T, args.steps, args.warmup, local)
         variants["near_balance"] = near_balance_workload(torch, T, n, params, R, args.steps, args.warmup, local)
     cb = None
     if not args.no_cpu_baseline:

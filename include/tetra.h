@@ -340,6 +340,34 @@ tetra_status_t tetra_spectral_t0(tetra_plan_t plan, const float *eps, const int 
                                  int n_omega, const float *omega, float *S, void *ws, size_t ws_bytes,
                                  cudaStream_t stream);
 
+/* Real part of the T = 0 bare susceptibility (the Lindhard-type extension of
+ * the method, abstract and Conclusions) at grid vector q:
+ *   Re chi0(q, w) = sum_{n,m} (1/V_G) P int dk [Theta(mu - e_n(k)) - Theta(mu - e_m(k+q))]
+ *                                          / (w - e_m(k+q) + e_n(k)),
+ * the Hilbert transform of tetra_spectral_t0's S (chi0 = int S(w')/(w - w' + i0) dw').
+ * Same clipping into sub-tetrahedra as tetra_spectral_t0; each sub-tetrahedron
+ * of volume fraction nu adds sign * nu * P<1/(w - D)>, the principal-value
+ * average of 1/(w - D) over it (D linear there): a moment series beyond four
+ * half-widths of its D range, the closed form of its density's three
+ * quadratic pieces (logarithms) nearer. Every sub-tetrahedron reaches every
+ * energy, so the cost grows with n_omega x sub-tetrahedra.
+ *   plan, eps, q, mu : as tetra_spectral_t0 (whole-grid plan, n_bands <= 8).
+ *   omega   : [n_omega] float, device, the energies (eV); any order.
+ *   R       : [n_omega] float, overwritten.
+ *   ws      : at least tetra_chi0_real_t0_workspace_bytes(plan, n_omega)
+ *             bytes, 16-byte aligned.
+ * The sub-tetrahedra of a warp are summed in FP32 in a fixed order (64 at a
+ * time) and added to exact 64-bit integer tiles: reproducible for a given
+ * plan and device, not bitwise independent of the launch shape. Returns
+ * TETRA_EINVAL for null/misaligned pointers, TETRA_EUNSUPPORTED for
+ * n_bands > 8, slab plans or n_omega beyond about 6000 (shared memory);
+ * device-side TETRA_ERANGE (tetra_workspace_status) for a sum beyond the
+ * 64-bit range. */
+size_t tetra_chi0_real_t0_workspace_bytes(tetra_plan_t plan, int n_omega);
+tetra_status_t tetra_chi0_real_t0(tetra_plan_t plan, const float *eps, const int q[3], float mu,
+                                  int n_omega, const float *omega, float *R, void *ws, size_t ws_bytes,
+                                  cudaStream_t stream);
+
 /* Device-side status recorded in a workspace by the last call that used it
  * (synchronises `stream`). TETRA_OK, TETRA_ETIMEOUT or TETRA_ERANGE. The
  * fixed-point accumulation of tetra_dos raises TETRA_ERANGE (and leaves that

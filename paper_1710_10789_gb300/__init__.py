@@ -28,7 +28,8 @@ __all__ = [
     "EXPORTED_SYMBOLS", "TetraTune", "tetra_plan_batched", "tetra_batch_plan_destroy",
     "tetra_batch_layout", "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
     "BatchPlan", "TETRA_MAX_BATCH", "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
-    "tetra_spectral_t0_workspace_bytes", "tetra_spectral_t0",
+    "tetra_spectral_t0_workspace_bytes", "tetra_spectral_t0", "tetra_chi0_real_t0_workspace_bytes",
+    "tetra_chi0_real_t0",
 ]
 
 TETRA_OK, TETRA_EINVAL, TETRA_EUNSUPPORTED, TETRA_ECUDA, TETRA_ENOMEM, TETRA_ETIMEOUT, TETRA_ERANGE = range(7)
@@ -45,7 +46,8 @@ EXPORTED_SYMBOLS = (
     "tetra_noalloc_status", "tetra_plan_batched", "tetra_batch_plan_destroy", "tetra_batch_layout",
     "tetra_batch_workspace_bytes", "tetra_batch_info", "tetra_dos_batched",
     "tetra_fermi_workspace_bytes", "tetra_fermi_level", "tetra_pair_bands",
-    "tetra_spectral_t0_workspace_bytes", "tetra_spectral_t0",
+    "tetra_spectral_t0_workspace_bytes", "tetra_spectral_t0", "tetra_chi0_real_t0_workspace_bytes",
+    "tetra_chi0_real_t0",
 )
 TETRA_MAX_BATCH = 64
 
@@ -136,6 +138,10 @@ def lib():
             L.tetra_spectral_t0_workspace_bytes.restype = sz
             L.tetra_spectral_t0.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_float, i, i, vp, vp,
                                             vp, sz, vp]
+            L.tetra_chi0_real_t0_workspace_bytes.argtypes = [vp, i]
+            L.tetra_chi0_real_t0_workspace_bytes.restype = sz
+            L.tetra_chi0_real_t0.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_float, i, vp, vp,
+                                             vp, sz, vp]
             L.tetra_strerror.argtypes = [i]
             L.tetra_strerror.restype = ctypes.c_char_p
             L.tetra_version.restype = ctypes.c_char_p
@@ -145,7 +151,7 @@ def lib():
                          "tetra_workspace_status", "tetra_plan_batched",
                          "tetra_batch_plan_destroy", "tetra_batch_layout", "tetra_batch_info",
                          "tetra_dos_batched", "tetra_fermi_level", "tetra_pair_bands",
-                         "tetra_spectral_t0"):
+                         "tetra_spectral_t0", "tetra_chi0_real_t0"):
                 getattr(L, name).restype = i
             _LIB = L
     return _LIB
@@ -207,6 +213,15 @@ def tetra_spectral_t0(plan, eps, q, mu, mode, n_omega, omega, S, ws, ws_bytes, s
     qa = (ctypes.c_int * 3)(*[int(v) for v in q])
     return lib().tetra_spectral_t0(plan, eps, qa, float(mu), int(mode), int(n_omega), omega, S, ws, ws_bytes,
                                    stream)
+
+
+def tetra_chi0_real_t0_workspace_bytes(plan, n_omega) -> int:
+    return int(lib().tetra_chi0_real_t0_workspace_bytes(plan, int(n_omega)))
+
+
+def tetra_chi0_real_t0(plan, eps, q, mu, n_omega, omega, R, ws, ws_bytes, stream) -> int:
+    qa = (ctypes.c_int * 3)(*[int(v) for v in q])
+    return lib().tetra_chi0_real_t0(plan, eps, qa, float(mu), int(n_omega), omega, R, ws, ws_bytes, stream)
 
 
 def tetra_noalloc_status(device, stream) -> int:
@@ -407,6 +422,22 @@ class Plan:
         ws = self._spec_ws
         _check(tetra_spectral_t0(self.handle, _ptr(eps), q, mu, m, n_om, _ptr(omega), _ptr(out), _ptr(ws),
                                  ws.numel(), _stream_handle(stream)), "tetra_spectral_t0")
+        return out
+
+    def chi0_real_t0(self, eps, q, mu, omega, out=None, stream=None):
+        """Real part of the T = 0 bare susceptibility at grid vector q
+        (tetra_chi0_real_t0) at the energies ``omega``. Returns Re chi0; its
+        device status is ``spectral_status()``."""
+        torch = _torch()
+        n_om = omega.numel()
+        if out is None:
+            out = torch.empty((n_om,), dtype=torch.float32, device=eps.device)
+        nbytes = tetra_chi0_real_t0_workspace_bytes(self.handle, n_om)
+        if getattr(self, "_spec_ws", None) is None or self._spec_ws.numel() < nbytes:
+            self._spec_ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=eps.device)
+        ws = self._spec_ws
+        _check(tetra_chi0_real_t0(self.handle, _ptr(eps), q, mu, n_om, _ptr(omega), _ptr(out), _ptr(ws),
+                                  ws.numel(), _stream_handle(stream)), "tetra_chi0_real_t0")
         return out
 
     def spectral_status(self, stream=None) -> int:
