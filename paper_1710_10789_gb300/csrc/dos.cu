@@ -275,8 +275,14 @@ __device__ __forceinline__ void tetp_setup(TetP &T, float e1, float e2, float e3
 // for the first case and (u r41, u r42, u r43, apex) for the third, so the
 // first and last outputs swap apex and u r41 and the middle two pick their
 // reciprocal: fewer selects than choosing every parameter first.
+// LEAN (the single-model kernel): the first case tested against the stored
+// e2c, and the mirrored forms' outputs picked as above. Otherwise (the
+// batched kernel, which has no register to spare for the leaner form: it
+// spilled there) the same values from the five selected parameters of the
+// case and one test E <= E2 and E < E4 (the same set as E <= e2c).
+template <bool LEAN = true>
 __device__ __forceinline__ void tetp_dw(const TetP &T, float E, float d[4]) {
-    const bool in1 = E <= T.e2c;
+    const bool in1 = LEAN ? E <= T.e2c : (E <= T.e2 && E < T.e4);
     const bool in3 = !in1 && E >= T.e3;
     const float v = fmaxf(in1 ? E - T.e1 : T.e4 - E, 0.f);
     const float P = in1 ? T.P1 : T.P3;
@@ -284,11 +290,21 @@ __device__ __forceinline__ void tetp_dw(const TetP &T, float E, float d[4]) {
     const float g = P * v * v;
     const float apex = g * fmaf(-v, S, 3.f);
     const float u = g * v;
-    const float u41 = u * T.r41;
-    const float m0 = in1 ? apex : u41;
-    const float m1 = u * (in1 ? T.r21 : T.r42);
-    const float m2 = u * (in1 ? T.r31 : T.r43);
-    const float m3 = in1 ? u41 : apex;
+    float m0, m1, m2, m3;
+    if constexpr (LEAN) {
+        const float u41 = u * T.r41;
+        m0 = in1 ? apex : u41;
+        m1 = u * (in1 ? T.r21 : T.r42);
+        m2 = u * (in1 ? T.r31 : T.r43);
+        m3 = in1 ? u41 : apex;
+    } else {
+        const float ra = in1 ? T.r21 : T.r41, rb = in1 ? T.r31 : T.r42, rc = in1 ? T.r41 : T.r43;
+        const float o1 = u * ra, o2 = u * rb, o3 = u * rc;
+        m0 = in1 ? apex : o1;
+        m1 = in1 ? o1 : o2;
+        m2 = in1 ? o2 : o3;
+        m3 = in1 ? o3 : apex;
+    }
     const float t = E - T.e2;
     float h[4];
 #pragma unroll
@@ -1009,8 +1025,8 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 // both tetrahedra's corner derivatives at E (zero outside a
                 // tetrahedron's own window (E1, E4), see tetp_dw)
                 auto both = [&](float E, float (&da)[4], float (&db)[4]) {
-                    tetp_dw(TA, E, da);
-                    tetp_dw(TB, E, db);
+                    tetp_dw<MAXM == 1>(TA, E, da);
+                    tetp_dw<MAXM == 1>(TB, E, db);
                 };
                 if (fast) {
                     // lane-dependent start, wrapping walk (see below)
@@ -1150,7 +1166,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     int i = lo + ((lane * K) >> 5);
                     for (int j = 0; j < K; ++j) {
                         float d[4];
-                        tetp_dw(TP, om[i - w0], d);
+                        tetp_dw<MAXM == 1>(TP, om[i - w0], d);
                         int *col = tile + (i - w0) * TS;
 #pragma unroll
                         for (int s = 0; s < NORB; ++s) {
@@ -1165,7 +1181,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 } else {
                     for (int i = lo; i <= hi; ++i) {
                         float d[4];
-                        tetp_dw(TP, om[i - w0], d);
+                        tetp_dw<MAXM == 1>(TP, om[i - w0], d);
                         deposit_slow<NORB>(b, d, A.n_orb, dith, Gc + (i - w0), A.chunk_w, A.status);
                     }
                 }
