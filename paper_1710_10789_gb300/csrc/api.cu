@@ -115,6 +115,16 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     if (d.mode == TETRA_INTEGRATED && P.n_chunks != 1) return TETRA_EUNSUPPORTED;
     P.chunk_w = (d.n_omega + P.n_chunks - 1) / P.n_chunks;
     P.smem_bytes = fixed + per_w * P.chunk_w + 8;
+    // Bin mode: neighbouring pairs of a band tend to fall into the same bin,
+    // so a warp's tile adds hit the same addresses; up to 8 copies of the
+    // tile (as shared memory allows), one per lane residue, spread them.
+    P.tile_copies = 1;
+    if (d.mode == TETRA_BIN && pairs) {
+        const size_t copy = 4 * (size_t)P.tile_stride * (P.chunk_w + 1);
+        const size_t room = P.smem_optin > P.smem_bytes ? P.smem_optin - P.smem_bytes : 0;
+        P.tile_copies = (int)std::min<size_t>(8, 1 + room / copy);
+        P.smem_bytes += (size_t)(P.tile_copies - 1) * copy;
+    }
     P.threads = pairs ? 384 : 512;
     const int ctas = std::max(1, ctas_per_sm) * P.sm_count;
     P.grid_x = std::max(1, std::min(P.n_boxes, (ctas + P.n_chunks - 1) / P.n_chunks));

@@ -115,6 +115,7 @@ struct FwdArgs {
     uint32_t e_box_bytes, w_box_bytes;   // TMA bytes of a box's energies / weights
     uint32_t e_stage, w_stage;           // their shared-memory slots (128-byte multiples)
     int chunk_w;         // energies per shared tile (largest model of a batch)
+    int tile_copies;     // copies of the tile; lane l of a bin-mode pair adds into copy l % tile_copies
     int items_per_box;   // items per box: (pair, band) in point mode, (tetrahedron, band) otherwise
     int fast_cap;
     unsigned flush_at;   // a 64-energy block is flushed once its bound reaches this
@@ -444,10 +445,13 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     // box's pass A and ranking run
     unsigned char *estage[2] = {smem, smem + A.e_stage};
     unsigned char *wstage = smem + 2 * A.e_stage;
-    int *tile = reinterpret_cast<int *>(wstage + A.w_stage);   // [chunk_w + 1][TS]
+    int *tile = reinterpret_cast<int *>(wstage + A.w_stage);   // [copies][chunk_w + 1][TS]
+    // (copies only for bin-mode pairs; elsewhere one, known at compile time)
+    constexpr bool kCopies = MODE == TETRA_BIN && Cfg<MODE, NORB>::pairs;
+    const int n_copies = kCopies ? A.tile_copies : 1, copy_ints = TS * (A.chunk_w + 1);
     // integrated mode: per-orbital sums of the saturated weights of the items
     // whose E4 lies between energy j-1 and j, [chunk_w][NORB] (plain integers)
-    int *stile = tile + TS * (A.chunk_w + 1);
+    int *stile = tile + copy_ints * n_copies;
     float *om = reinterpret_cast<float *>(stile + (MODE == TETRA_INTEGRATED ? NORB * A.chunk_w : 0));
     float *iw = om + A.chunk_w + 1;                                   // 1/bin width (bin mode)
     unsigned *blk_bound = reinterpret_cast<unsigned *>(iw + (MODE == TETRA_BIN ? A.chunk_w : 0));
@@ -563,7 +567,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     // to per-row add counts by a block-wide inclusive scan, and back. Each
     // warp scans a segment of rows; segment totals are combined through
     // shared memory. Called by every thread of the CTA.
-    auto counts_from_diffs = [&]() {
+    auto counts_from_diffs = [&](int *tile) {
         const int nw = (int)(blockDim.x >> 5), warp = tid >> 5, lane = tid & 31;
         const int nr = wc + 1;
         const int seg = ((nr + nw - 1) / nw + 31) & ~31;
@@ -589,7 +593,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             for (int rr = r0 + lane; rr < r1; rr += 32) tile[rr * TS + CNT] += off;
         __syncthreads();
     };
-    auto diffs_from_counts = [&]() {
+    auto diffs_from_counts = [&](int *tile) {
         const int nw = (int)(blockDim.x >> 5), warp = tid >> 5, lane = tid & 31;
         const int nr = wc + 1;
         const int seg = ((nr + nw - 1) / nw + 31) & ~31;
@@ -611,17 +615,23 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     };
     // Value of a tile entry since its last flush: raw sum minus count * M
     // (modulo 2^32; the bounds keep the true value below 2^31 in magnitude).
-    auto entry_value = [&](int j, int s) -> int {
+    auto entry_value = [&](const int *tile, int j, int s) -> int {
         const unsigned n_add = (unsigned)tile[j * TS + CNT];
         return (int)((unsigned)tile[j * TS + s] - n_add * (unsigned)kMagicBits);
+    };
+    // the entry's value summed over the tile's copies
+    auto entry_total = [&](int j, int s) -> int {
+        int v = 0;
+        for (int c = 0; c < n_copies; ++c) v += entry_value(tile + c * copy_ints, j, s);
+        return v;
     };
     // moves the int32 tile of the current model into its int64 partial slot
     long long *Gsc = A.Gs;
     auto flush_tile = [&]() {
-        counts_from_diffs();
+        for (int c = 0; c < n_copies; ++c) counts_from_diffs(tile + c * copy_ints);
         for (int i = tid; i < A.n_orb * wc; i += blockDim.x) {
             const int s = i / wc, j = i - s * wc;
-            const int v = entry_value(j, s);
+            const int v = entry_total(j, s);
             if (v)
                 atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j),
                           static_cast<unsigned long long>(static_cast<long long>(v)));
@@ -651,7 +661,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             const long slot = (MAXM == 1) ? (long)chunk * gridDim.x + blockIdx.x : (long)mi;
             Gc = A.G + slot * (long)A.n_orb * A.chunk_w;
             if (MODE == TETRA_INTEGRATED) Gsc = A.Gs + slot * (long)A.n_orb * A.chunk_w;
-            for (int i = tid; i < TS * (A.chunk_w + 1); i += blockDim.x) tile[i] = 0;
+            for (int i = tid; i < copy_ints * n_copies; i += blockDim.x) tile[i] = 0;
             if (MODE == TETRA_INTEGRATED)
                 for (int i = tid; i < NORB * A.chunk_w; i += blockDim.x) stile[i] = 0;
             for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
@@ -962,11 +972,13 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     float qmax = bmax * 8.f * fq * max_iw * 1.01f;
                     if (!(ea[3] > ea[0]) || !(eb[3] > eb[0])) qmax = 3.0e38f;
                     const bool fast = qmax < (float)A.fast_cap;
+                    // this lane's copy of the tile (the copies are summed when flushed)
+                    int *tl = tile + (n_copies > 1 ? (lane % n_copies) * copy_ints : 0);
                     if (fast && hi >= lo) {
                         const unsigned qbnd = (unsigned)qmax + 2u;
                         for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
-                        atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
-                        atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
+                        atomicAdd(&tl[(lo - w0) * TS + CNT], 1);
+                        atomicAdd(&tl[(hi + 1 - w0) * TS + CNT], -1);
                     }
                     Tet TA, TB;
                     tet_setup(TA, ea[0], ea[1], ea[2], ea[3], fq);
@@ -974,7 +986,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     float wpa[4], wpb[4];
                     tet_weights(TA, om[lo - w0], wpa);
                     tet_weights(TB, om[lo - w0], wpb);
-                    int *col = tile + (lo - w0) * TS;
+                    int *col = tl + (lo - w0) * TS;
                     for (int i = lo; i <= hi; ++i, col += TS) {
                         float wna[4], wnb[4], da[4], db[4];
                         tet_weights(TA, om[i + 1 - w0], wna);
@@ -1226,18 +1238,20 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         // A flushed entry is reset to count * M, the raw value of zero.
         const bool mine = tid < n_blk && blk_bound[tid] >= A.flush_at;
         if (__syncthreads_or(mine)) {
-            counts_from_diffs();
+            for (int c = 0; c < n_copies; ++c) counts_from_diffs(tile + c * copy_ints);
             for (int bk = 0; bk < n_blk; ++bk) {
                 if (blk_bound[bk] < A.flush_at) continue;   // uniform: every thread reads the same value
                 const int j0 = bk << 6, jn = min(64, wc - j0);
                 for (int i = tid; i < A.n_orb * 64; i += blockDim.x) {
                     const int s = i >> 6, j = i & 63;
                     if (j >= jn) continue;
-                    const int v = entry_value(j0 + j, s);
-                    if (v) {
+                    const int v = entry_total(j0 + j, s);
+                    if (v)
                         atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j0 + j),
                                   static_cast<unsigned long long>(static_cast<long long>(v)));
-                        tile[(j0 + j) * TS + s] = (int)((unsigned)tile[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
+                    for (int c = 0; c < n_copies; ++c) {
+                        int *tc = tile + c * copy_ints;
+                        tc[(j0 + j) * TS + s] = (int)((unsigned)tc[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
                     }
                     if (MODE == TETRA_INTEGRATED) {
                         int *se = &stile[(j0 + j) * NORB + s];
@@ -1250,7 +1264,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                 }
             }
             __syncthreads();
-            diffs_from_counts();
+            for (int c = 0; c < n_copies; ++c) diffs_from_counts(tile + c * copy_ints);
             if (tid < n_blk && blk_bound[tid] >= A.flush_at) blk_bound[tid] = 0;
             __syncthreads();
         }
@@ -1403,6 +1417,7 @@ void fill_common(const Plan &P, FwdArgs &A) {
     A.e_stage = (A.e_box_bytes + 127u) & ~127u;
     A.w_stage = (A.w_box_bytes + 127u) & ~127u;
     A.chunk_w = P.chunk_w;
+    A.tile_copies = P.tile_copies;
     A.items_per_box = P.items_per_box;
     A.flush_at = 1u << P.flush_bits;
     long cap = ((1L << 30) - (1L << 20)) / A.items_per_box;

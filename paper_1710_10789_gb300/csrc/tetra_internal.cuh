@@ -28,6 +28,7 @@ struct tetra_plan_s {
     int flush_bits;             // a tile block is flushed once its bound reaches 2^flush_bits
     int items_per_box;          // work units per box: (pair, band) in point mode, (tetrahedron, band) in bin mode
     int tile_stride;            // ints per energy in the shared tile
+    int tile_copies;            // copies of the tile (bin mode: lanes spread over them)
     size_t smem_bytes;
 };
 
