@@ -118,9 +118,10 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     // Bin mode: neighbouring pairs of a band tend to fall into the same bin,
     // so a warp's tile adds hit the same addresses; up to 8 copies of the
     // tile (as shared memory allows), one per lane residue, spread them.
+    // Each copy has its own block bounds (4 bytes per 64 energies).
     P.tile_copies = 1;
     if (d.mode == TETRA_BIN && pairs) {
-        const size_t copy = 4 * (size_t)P.tile_stride * (P.chunk_w + 1);
+        const size_t copy = 4 * (size_t)P.tile_stride * (P.chunk_w + 1) + 4 * (size_t)((P.chunk_w + 63) / 64);
         const size_t room = P.smem_optin > P.smem_bytes ? P.smem_optin - P.smem_bytes : 0;
         P.tile_copies = (int)std::min<size_t>(8, 1 + room / copy);
         P.smem_bytes += (size_t)(P.tile_copies - 1) * copy;

@@ -456,7 +456,8 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     float *iw = om + A.chunk_w + 1;                                   // 1/bin width (bin mode)
     unsigned *blk_bound = reinterpret_cast<unsigned *>(iw + (MODE == TETRA_BIN ? A.chunk_w : 0));
     const int n_blk = (A.chunk_w + 63) >> 6;
-    short *s_lo = reinterpret_cast<short *>(blk_bound + n_blk);      // window start - w0
+    // (one set of block bounds per tile copy: copy c's bounds at c * n_blk)
+    short *s_lo = reinterpret_cast<short *>(blk_bound + n_blk * n_copies);   // window start - w0
     unsigned short *s_K = reinterpret_cast<unsigned short *>(s_lo + A.items_per_box);
     unsigned short *s_list = s_K + A.items_per_box;                 // items sorted by K
     int *khist = reinterpret_cast<int *>(
@@ -664,7 +665,7 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             for (int i = tid; i < copy_ints * n_copies; i += blockDim.x) tile[i] = 0;
             if (MODE == TETRA_INTEGRATED)
                 for (int i = tid; i < NORB * A.chunk_w; i += blockDim.x) stile[i] = 0;
-            for (int i = tid; i < n_blk; i += blockDim.x) blk_bound[i] = 0;
+            for (int i = tid; i < n_blk * n_copies; i += blockDim.x) blk_bound[i] = 0;
             const int n_om = (MODE != TETRA_BIN) ? wc : wc + 1;
             for (int i = tid; i < n_om; i += blockDim.x) om[i] = M.omega[w0 + i];
             __syncthreads();
@@ -972,11 +973,14 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     float qmax = bmax * 8.f * fq * max_iw * 1.01f;
                     if (!(ea[3] > ea[0]) || !(eb[3] > eb[0])) qmax = 3.0e38f;
                     const bool fast = qmax < (float)A.fast_cap;
-                    // this lane's copy of the tile (the copies are summed when flushed)
-                    int *tl = tile + (n_copies > 1 ? (lane % n_copies) * copy_ints : 0);
+                    // this lane's copy of the tile and of its block bounds (the
+                    // copies are summed when flushed)
+                    const int cp = n_copies > 1 ? lane % n_copies : 0;
+                    int *tl = tile + cp * copy_ints;
+                    unsigned *bl = blk_bound + cp * n_blk;
                     if (fast && hi >= lo) {
                         const unsigned qbnd = (unsigned)qmax + 2u;
-                        for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
+                        for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&bl[bk], qbnd);
                         atomicAdd(&tl[(lo - w0) * TS + CNT], 1);
                         atomicAdd(&tl[(hi + 1 - w0) * TS + CNT], -1);
                     }
@@ -1236,36 +1240,43 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         // partial before the next box: one box adds less than 2^30 - 2^20 to any
         // entry (per-unit cap x units per box), so entries stay below 2^31.
         // A flushed entry is reset to count * M, the raw value of zero.
-        const bool mine = tid < n_blk && blk_bound[tid] >= A.flush_at;
+        bool mine = false;
+        for (int i = tid; i < n_blk * n_copies; i += blockDim.x) mine = mine || blk_bound[i] >= A.flush_at;
         if (__syncthreads_or(mine)) {
-            for (int c = 0; c < n_copies; ++c) counts_from_diffs(tile + c * copy_ints);
-            for (int bk = 0; bk < n_blk; ++bk) {
-                if (blk_bound[bk] < A.flush_at) continue;   // uniform: every thread reads the same value
-                const int j0 = bk << 6, jn = min(64, wc - j0);
-                for (int i = tid; i < A.n_orb * 64; i += blockDim.x) {
-                    const int s = i >> 6, j = i & 63;
-                    if (j >= jn) continue;
-                    const int v = entry_total(j0 + j, s);
-                    if (v)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j0 + j),
-                                  static_cast<unsigned long long>(static_cast<long long>(v)));
-                    for (int c = 0; c < n_copies; ++c) {
-                        int *tc = tile + c * copy_ints;
-                        tc[(j0 + j) * TS + s] = (int)((unsigned)tc[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
-                    }
-                    if (MODE == TETRA_INTEGRATED) {
-                        int *se = &stile[(j0 + j) * NORB + s];
-                        if (*se) {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(Gsc + (long)s * A.chunk_w + j0 + j),
-                                      static_cast<unsigned long long>(static_cast<long long>(*se)));
-                            *se = 0;
+            for (int c = 0; c < n_copies; ++c) {
+                const unsigned *bc = blk_bound + c * n_blk;
+                bool any = false;   // uniform: every thread reads the same values
+                for (int bk = 0; bk < n_blk; ++bk) any = any || bc[bk] >= A.flush_at;
+                if (!any) continue;
+                int *tc = tile + c * copy_ints;
+                counts_from_diffs(tc);
+                for (int bk = 0; bk < n_blk; ++bk) {
+                    if (bc[bk] < A.flush_at) continue;   // uniform
+                    const int j0 = bk << 6, jn = min(64, wc - j0);
+                    for (int i = tid; i < A.n_orb * 64; i += blockDim.x) {
+                        const int s = i >> 6, j = i & 63;
+                        if (j >= jn) continue;
+                        const int v = entry_value(tc, j0 + j, s);
+                        if (v) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j0 + j),
+                                      static_cast<unsigned long long>(static_cast<long long>(v)));
+                            tc[(j0 + j) * TS + s] = (int)((unsigned)tc[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
+                        }
+                        if (MODE == TETRA_INTEGRATED) {
+                            int *se = &stile[(j0 + j) * NORB + s];
+                            if (*se) {
+                                atomicAdd(reinterpret_cast<unsigned long long *>(Gsc + (long)s * A.chunk_w + j0 + j),
+                                          static_cast<unsigned long long>(static_cast<long long>(*se)));
+                                *se = 0;
+                            }
                         }
                     }
                 }
+                __syncthreads();
+                diffs_from_counts(tc);
             }
-            __syncthreads();
-            for (int c = 0; c < n_copies; ++c) diffs_from_counts(tile + c * copy_ints);
-            if (tid < n_blk && blk_bound[tid] >= A.flush_at) blk_bound[tid] = 0;
+            for (int i = tid; i < n_blk * n_copies; i += blockDim.x)
+                if (blk_bound[i] >= A.flush_at) blk_bound[i] = 0;
             __syncthreads();
         }
     }
