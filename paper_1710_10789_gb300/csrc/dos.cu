@@ -446,8 +446,9 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
     unsigned char *estage[2] = {smem, smem + A.e_stage};
     unsigned char *wstage = smem + 2 * A.e_stage;
     int *tile = reinterpret_cast<int *>(wstage + A.w_stage);   // [copies][chunk_w + 1][TS]
-    // (copies only for bin-mode pairs; elsewhere one, known at compile time)
-    constexpr bool kCopies = MODE == TETRA_BIN && Cfg<MODE, NORB>::pairs;
+    // (copies only for single-model bin-mode pairs; elsewhere one, known at
+    // compile time: the batched kernel measured faster without them)
+    constexpr bool kCopies = MODE == TETRA_BIN && Cfg<MODE, NORB>::pairs && MAXM == 1;
     const int n_copies = kCopies ? A.tile_copies : 1, copy_ints = TS * (A.chunk_w + 1);
     // integrated mode: per-orbital sums of the saturated weights of the items
     // whose E4 lies between energy j-1 and j, [chunk_w][NORB] (plain integers)
@@ -1240,6 +1241,32 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
         // partial before the next box: one box adds less than 2^30 - 2^20 to any
         // entry (per-unit cap x units per box), so entries stay below 2^31.
         // A flushed entry is reset to count * M, the raw value of zero.
+        if constexpr (MAXM > 1) {
+            // (the batched kernel: one tile copy; this form measured faster there)
+            const bool mine = tid < n_blk && blk_bound[tid] >= A.flush_at;
+            if (__syncthreads_or(mine)) {
+                counts_from_diffs(tile);
+                for (int bk = 0; bk < n_blk; ++bk) {
+                    if (blk_bound[bk] < A.flush_at) continue;   // uniform: every thread reads the same value
+                    const int j0 = bk << 6, jn = min(64, wc - j0);
+                    for (int i = tid; i < A.n_orb * 64; i += blockDim.x) {
+                        const int s = i >> 6, j = i & 63;
+                        if (j >= jn) continue;
+                        const int v = entry_value(tile, j0 + j, s);
+                        if (v) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(Gc + (long)s * A.chunk_w + j0 + j),
+                                      static_cast<unsigned long long>(static_cast<long long>(v)));
+                            tile[(j0 + j) * TS + s] = (int)((unsigned)tile[(j0 + j) * TS + CNT] * (unsigned)kMagicBits);
+                        }
+                    }
+                }
+                __syncthreads();
+                diffs_from_counts(tile);
+                if (tid < n_blk && blk_bound[tid] >= A.flush_at) blk_bound[tid] = 0;
+                __syncthreads();
+            }
+            continue;
+        }
         bool mine = false;
         for (int i = tid; i < n_blk * n_copies; i += blockDim.x) mine = mine || blk_bound[i] >= A.flush_at;
         if (__syncthreads_or(mine)) {
