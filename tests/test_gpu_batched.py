@@ -73,6 +73,9 @@ SMALL = [((9, 7, 6), 120, (0.0, 1.0)), ((16, 16, 16), 401, (0.0, 1.0)),
 @pytest.mark.parametrize("wdtype", ["f32", "bf16"])
 @pytest.mark.parametrize("mode", ["point", "bin"])
 def test_small_batch_matches_single_and_oracle(T, mode, wdtype):
+    # (in bin mode the single-model launch spreads its tile adds over several
+    # copies of the tile and the batch uses one: equal bits also check the
+    # copies' add counts and flushes)
     specs = [s for s in SMALL if not (mode == "bin" and s[1] == 1)]
     probs = [tb_problem(40 + i, n) for i, (n, _, _) in enumerate(specs)]
     plan = T.BatchPlan([s[0] for s in specs], [s[1] for s in specs], 8, 8, mode=mode,
