@@ -203,8 +203,8 @@ tetra_status_t tetra_eig(tetra_plan_t plan, const tetra_model_t *model, float *e
  * paper): given dL/d eps and dL/d w in the tetra layout (float; halo entries
  * ignored), writes grad_params (same packing as model->params, float).
  * Eigenvector derivatives use F_nm = d/(d^2 + eta^2), d = e_n - e_m,
- * eta = 1e-8 eV, in FP32 (d is exact for eigenvalues within a factor two of
- * each other, so nearly degenerate pairs lose nothing). Deterministic: fixed
+ * eta = 1e-8 eV, in FP64 for near-degenerate pairs (|d| < 1e-4 eV) and in
+ * FP32 for the rest. Deterministic: fixed
  * summation order over k-points and blocks. Needs
  * tetra_eig_workspace_bytes(plan) bytes of workspace. */
 tetra_status_t tetra_eig_backward(tetra_plan_t plan, const tetra_model_t *model,

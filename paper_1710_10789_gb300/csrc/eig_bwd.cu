@@ -7,9 +7,9 @@
 // so that dL = Re sum_ij dH_ij Q_ij with
 //   Q = conj(V) (diag(geps) + 2 B) V^T,  B_mn = F_nm sum_s gw_{n s} conj(V_sn) V_sm.
 // F_nm is regularised as d / (d^2 + eta^2), d = eps_n - eps_m, eta = 1e-8 eV,
-// so near-degenerate pairs stay finite; it is formed in FP32 (d is exact when
-// the two eigenvalues are within a factor two of each other, so nearly equal
-// pairs lose nothing). With H(k) = diag(onsite) + sum_r [t_r e^{ik.R_r} + h.c.]:
+// so near-degenerate pairs stay finite; for those (|d| < kNearDeg) it is
+// formed in FP64, for the rest in FP32 (their 1/d is far from any
+// cancellation). With H(k) = diag(onsite) + sum_r [t_r e^{ik.R_r} + h.c.]:
 //   dL/d onsite_i = Re sum_k Q_ii,
 //   dL/d Re t_r   = Re sum_k e^{ik.R_r} (Q + Q^H),   dL/d Im t_r = -Im (same).
 // Each persistent block takes kBT k-points per step, one per thread, and adds
@@ -38,6 +38,8 @@ constexpr int kBT = 128;     // k-points per block step
 constexpr int kChunk = 32;   // k-points summed in FP32 before an FP64 add
 constexpr int kRB = 4;       // lattice vectors per reduction pass of a thread
 constexpr float kEta2 = 1e-16f;   // eta^2, eta = 1e-8 eV
+constexpr double kEta = 1e-8;
+constexpr float kNearDeg = 1e-4f; // eV: pairs this close take F_nm in FP64
 
 struct EigBwdArgs {
     int n1, n2, n3, nx, ny, n_R;
@@ -48,6 +50,14 @@ struct EigBwdArgs {
     double *partial;   // [gridDim.x][n_out]
     int n_out;
 };
+
+// 2 F_nm in FP64 for a near-degenerate pair; one copy of the code, called
+// from the unrolled pair loop (inline, its 28 FP64 divisions would crowd the
+// instruction cache).
+__device__ __noinline__ float twice_f_fp64(float en, float em) {
+    const double dd = (double)en - (double)em;
+    return (float)(2.0 * dd / (dd * dd + kEta * kEta));
+}
 
 template <int N>
 __host__ __device__ constexpr int row_floats() { return 2 * N * N + 1; }
@@ -192,7 +202,11 @@ __global__ void __launch_bounds__(kBT, 2) tetra_eig_bwd_kernel(const EigBwdArgs 
 #pragma unroll
                 for (int m = 0; m < n; ++m) {
                     const float d = lam[n] - lam[m];
-                    const float F2 = 2.f * __fdividef(d, fmaf(d, d, kEta2));
+                    float F2 = 2.f * __fdividef(d, fmaf(d, d, kEta2));
+                    // FP64 only in a warp that has a near-degenerate pair here
+                    // (a vote, so the rare FP64 path is not evaluated for all)
+                    if (__any_sync(__activemask(), fabsf(d) < kNearDeg) && fabsf(d) < kNearDeg)
+                        F2 = twice_f_fp64(lam[n], lam[m]);
                     sr[m][n] *= F2;
                     si[m][n] *= F2;
                 }
