@@ -341,3 +341,19 @@ def test_paper_shape_five_projected_orbitals(T):
     r = oracle.dos(E_h, W_h, *n, om.cpu().numpy().astype(np.float64), nthreads=NTHREADS)
     assert g.shape == (5, 1024)
     assert_parity(g, r)
+
+
+@pytest.mark.parametrize("how", ["swap_xz", "invert"])
+def test_gpu_invariant_under_maps_of_the_triangulation(T, how):
+    """Swapping the x and z axes, or inverting k, maps Table I's
+    triangulation onto itself with every tetrahedron's corners in another
+    order: the GPU's DOS of the relabelled grid equals the original within
+    the parity bar (not bit for bit: the rounding dither is keyed to the
+    tetrahedron's place in its cube, which the map changes)."""
+    from test_oracle_pins import grid_map
+    n = (12, 10, 12)
+    _, eps, w = tb_problem(9, n)
+    omega = energy_window(eps, 300)
+    g0, *_ = run_gpu(T, eps, w, n, omega)
+    g1, *_ = run_gpu(T, grid_map(eps, n, how), grid_map(w, n, how), n, omega)
+    assert_parity(g1, g0)

@@ -835,3 +835,49 @@ def test_chi0_real_is_the_hilbert_transform_of_s():
     m1 = float(np.sum(s * 0.5 * (lo + hi) * (hi - lo)))
     rb = oracle.chi0_real_t0(eps, *n, q, mu, big)
     np.testing.assert_allclose(rb * big ** 2, m1, rtol=2e-2)
+
+
+# ---- corner-permutation invariance ------------------------------------------
+
+def grid_map(a, n, how):
+    """Relabel the k-grid of per-point data a (nk, ...) in x-fastest order:
+    "swap_xz" k' = (z, y, x) (needs n1 == n3), "invert" k' = -k (periodic)."""
+    n1, n2, n3 = n
+    A = a.reshape((n3, n2, n1) + a.shape[1:])          # [z][y][x]
+    if how == "swap_xz":
+        B = np.swapaxes(A, 0, 2)
+    else:
+        B = np.roll(np.flip(A, axis=(0, 1, 2)), 1, axis=(0, 1, 2))
+    return np.ascontiguousarray(B).reshape(a.shape)
+
+
+@pytest.mark.parametrize("how", ["swap_xz", "invert"])
+@pytest.mark.parametrize("mode", ["point", "bin"])
+def test_dos_invariant_under_maps_of_the_triangulation(how, mode):
+    """Table I's six tetrahedra share the cube diagonal from corner (0,1,0) to
+    (1,0,1); swapping the x and z axes, or inverting k, maps that
+    triangulation onto itself with every tetrahedron's corners in another
+    order. The DOS must not change: the corner sort and the weight-to-corner
+    bookkeeping are order independent (corner-permutation invariance)."""
+    n = (4, 3, 4)
+    rng = np.random.default_rng(77)
+    nk = n[0] * n[1] * n[2]
+    eps = np.sort(rng.normal(0, 1, (nk, 3)), axis=1)
+    w = rng.uniform(0.05, 1, (nk, 3, 2))
+    edges = np.linspace(eps.min() - 0.2, eps.max() + 0.2, 41)
+    om = edges if mode == "bin" else 0.5 * (edges[1:] + edges[:-1])
+    d0 = oracle.dos(eps, w, *n, om, mode=mode)
+    d1 = oracle.dos(grid_map(eps, n, how), grid_map(w, n, how), *n, om, mode=mode)
+    np.testing.assert_allclose(d1, d0, rtol=0, atol=1e-12 * np.max(np.abs(d0)))
+    # a relabelling that moves the diagonal (swapping x and y) does change
+    # the DOS at this resolution, so the check has teeth
+    m = (4, 4, 4)
+    e4 = np.sort(rng.normal(0, 1, (64, 3)), axis=1)
+    w4 = rng.uniform(0.05, 1, (64, 3, 2))
+    A = e4.reshape(4, 4, 4, 3)
+    Wa = w4.reshape(4, 4, 4, 3, 2)
+    exy = np.ascontiguousarray(np.swapaxes(A, 1, 2)).reshape(64, 3)
+    wxy = np.ascontiguousarray(np.swapaxes(Wa, 1, 2)).reshape(64, 3, 2)
+    f0 = oracle.dos(e4, w4, *m, om, mode=mode)
+    f1 = oracle.dos(exy, wxy, *m, om, mode=mode)
+    assert np.max(np.abs(f1 - f0)) > 1e-6 * np.max(np.abs(f0))
