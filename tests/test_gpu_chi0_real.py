@@ -104,3 +104,29 @@ def test_chi0_real_from_the_model_at_64cube(T):
     err = np.max(np.abs(r[idx] - ref)) / np.max(np.abs(ref))
     print(f"64^3 Re chi0 at 6 energies: max rel err {err:.2e}")
     assert err <= TOL
+
+
+def test_chi0_real_near_the_energy_limit_and_beyond(T):
+    """6000 energies (near the shared-memory limit of about 6300: the per-warp
+    FP32 sums hold every energy) against the oracle at sampled energies; one
+    energy more than fits is refused with TETRA_EUNSUPPORTED before any
+    launch; and the T = 0 spectral function is refused the same way beyond
+    its own limit."""
+    n = (6, 5, 4)
+    _, eps, _ = tb_problem(3, n)
+    mu = float(np.median(eps))
+    omega = tbgen.uniform_grid(-4.0, 4.0, 6000)
+    g, plan, Et, _ = gpu_real(T, eps, n, (1, 2, 0), mu, omega)
+    idx = np.linspace(0, 5999, 9).astype(int)
+    r = oracle.chi0_real_t0(eps.astype(np.float64), *n, (1, 2, 0), mu, omega[idx].astype(np.float64),
+                            nthreads=NTHREADS)
+    assert np.max(np.abs(g[idx] - r)) <= TOL * np.max(np.abs(r))
+    dev = Et.device
+    big = torch.from_numpy(tbgen.uniform_grid(-4.0, 4.0, 7000)).to(dev)
+    with pytest.raises(T.TetraError) as ex:
+        plan.chi0_real_t0(Et, (1, 2, 0), mu, big)
+    assert ex.value.status == T.TETRA_EUNSUPPORTED
+    huge = torch.from_numpy(tbgen.uniform_grid(-4.0, 4.0, 20000)).to(dev)
+    with pytest.raises(T.TetraError) as ex:
+        plan.spectral_t0(Et, (1, 2, 0), mu, huge)
+    assert ex.value.status == T.TETRA_EUNSUPPORTED
