@@ -42,10 +42,13 @@ OPS_PER_ITEM = 40
 # DRAM bytes (read + write) of one tetra_dos_fwd_kernel launch from an ncu
 # capture of the 128^3, 4000-energy, FP32, point-mode launch, scaled by the
 # number of boxes to other cubic grids (the traffic is per box: halo reads of
-# the TMA boxes). Valid only for the kernel source it was taken from (first 16
-# hex digits of the SHA-256 of csrc/dos.cu); otherwise the bench reports null.
-DOS_TRAFFIC_CAPTURE = {"dos_cu_sha256": "8923e50e6baab7ac", "grid": 128, "n_omega": 4000,
+# the TMA boxes). Valid only for the kernel source it was taken from: first 16
+# hex digits of the SHA-256 of csrc/dos.cu up to the reduce kernels (the
+# forward kernel and every device function it calls); otherwise the bench
+# reports null.
+DOS_TRAFFIC_CAPTURE = {"dos_fwd_sha256": "b897e6a8160c7f30", "grid": 128, "n_omega": 4000,
                        "bytes": 692142848 + 4363264}
+DOS_FWD_END = b"// Single model: dos[s][w0+j] = u * sum over CTAs of the int64 partials (exact)."
 
 
 def parse():
@@ -176,8 +179,10 @@ def dos_traffic(n, n_omega, mode, weight_dtype):
     import hashlib
     c = DOS_TRAFFIC_CAPTURE
     src = os.path.join(ROOT, "paper_1710_10789_gb300", "csrc", "dos.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if sha != c["dos_cu_sha256"] or n_omega != c["n_omega"] or mode != "point" or weight_dtype != "f32":
+    text = open(src, "rb").read()
+    end = text.find(DOS_FWD_END)
+    sha = hashlib.sha256(text[:end]).hexdigest()[:16] if end > 0 else None
+    if sha != c["dos_fwd_sha256"] or n_omega != c["n_omega"] or mode != "point" or weight_dtype != "f32":
         return None
     return c["bytes"] * (n / c["grid"]) ** 3
 

@@ -112,9 +112,10 @@ size_t tetra_workspace_bytes(tetra_plan_t plan);
  *                           the occupation of orbital s per spin up to E_i
  *                           (Eq. (2) with the step function as occupation;
  *                           not in the paper, which integrates the DOS only).
- *                           The whole energy grid must fit one shared-memory
- *                           tile (about 2400 energies for 8 orbitals; the plan
- *                           returns TETRA_EUNSUPPORTED otherwise).
+ *                           Grids longer than one shared-memory tile (about
+ *                           2400 energies for 8 orbitals) run as several
+ *                           energy chunks; every value is the same integer sum
+ *                           as in a plan over that energy alone.
  *            Normalised per spin and orbital: with unitary weights the bin
  *            DOS of each orbital integrates to 1, and n_s(E) rises from 0 to 1.
  *   ws     : device workspace of at least tetra_workspace_bytes(plan) bytes,

@@ -111,8 +111,6 @@ static tetra_status_t plan_geometry(Plan &P, const int box[3], int ctas_per_sm) 
     if (fixed + per_w * 64 > P.smem_optin) return TETRA_EUNSUPPORTED;
     int cw = (int)std::min<size_t>((P.smem_optin - fixed - 8) / per_w, (size_t)d.n_omega);
     P.n_chunks = (d.n_omega + cw - 1) / cw;
-    // the integrated mode's steps reach every later energy: one chunk only
-    if (d.mode == TETRA_INTEGRATED && P.n_chunks != 1) return TETRA_EUNSUPPORTED;
     P.chunk_w = (d.n_omega + P.n_chunks - 1) / P.n_chunks;
     P.smem_bytes = fixed + per_w * P.chunk_w + 8;
     // Bin mode: neighbouring pairs of a band tend to fall into the same bin,

@@ -1337,25 +1337,31 @@ __global__ void tetra_dos_reduce_kernel(const long long *G, int grid_x, int n_or
     }
 }
 
-// Integrated mode (one energy chunk): block s = orbital s;
-// dos[s][i] = u * (sum over CTAs of the window partials at i + the running sum
-// over i' <= i of the step partials), exact int64 arithmetic up to the scaling.
+// Integrated mode: block (s, c) = orbital s, energy chunk c. A chunk's CTAs
+// put the steps of every tetrahedron below the chunk on its first energy, so
+// the running sum of the step partials starts afresh in each chunk:
+// dos[s][w0 + j] = u * (sum over CTAs of the window partials at j + the
+// running sum over j' <= j of the chunk's step partials), exact int64
+// arithmetic up to the scaling.
 __global__ void tetra_dos_reduce_integrated(const long long *G, const long long *Gs, int grid_x, int n_orb,
                                             int n_omega, int chunk_w, const float *omega, double vtvg,
                                             int bits, float *dos) {
     __shared__ long long s_warp[32];
     __shared__ long long s_carry;
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = blockIdx.x, chunk = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = (int)(blockDim.x >> 5);
+    const int w0 = chunk * chunk_w, wc = min(chunk_w, n_omega - w0);
+    const long cta_stride = (long)n_orb * chunk_w;
+    const long first = ((long)chunk * grid_x * n_orb + s) * chunk_w;
     const double u = fixed_unit(omega, n_omega, TETRA_INTEGRATED, vtvg, bits);
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < n_omega; base += blockDim.x) {
-        const int i = base + tid;
+    for (int base = 0; base < wc; base += blockDim.x) {
+        const int j = base + tid;
         long long wsum = 0, ssum = 0;
-        if (i < n_omega) {
+        if (j < wc) {
             for (int c = 0; c < grid_x; ++c) {
-                const long off = ((long)c * n_orb + s) * chunk_w + i;
+                const long off = first + c * cta_stride + j;
                 wsum += G[off];
                 ssum += Gs[off];
             }
@@ -1371,7 +1377,7 @@ __global__ void tetra_dos_reduce_integrated(const long long *G, const long long 
         long long off = s_carry;
         for (int w2 = 0; w2 < warp; ++w2) off += s_warp[w2];
         x += off;
-        if (i < n_omega) dos[(long)s * n_omega + i] = (float)((double)(wsum + x) * u);
+        if (j < wc) dos[(long)s * n_omega + w0 + j] = (float)((double)(wsum + x) * u);
         __syncthreads();
         if (tid == 0) {
             long long tot = 0;
@@ -1524,9 +1530,10 @@ tetra_status_t launch_dos_forward(const Plan &P, const float *eps, const void *w
                                                                A, stream);
     if (e != cudaSuccess) return TETRA_ECUDA;
     if (mode == TETRA_INTEGRATED) {
-        tetra_dos_reduce_integrated<<<P.d.n_orb, 256, 0, stream>>>(A.G, A.Gs, P.grid_x, P.d.n_orb, P.d.n_omega,
-                                                                   P.chunk_w, omega, Bt.m[0].vtvg,
-                                                                   P.fixed_bits, dos);
+        const dim3 rgrid(P.d.n_orb, P.n_chunks);
+        tetra_dos_reduce_integrated<<<rgrid, 256, 0, stream>>>(A.G, A.Gs, P.grid_x, P.d.n_orb, P.d.n_omega,
+                                                               P.chunk_w, omega, Bt.m[0].vtvg, P.fixed_bits,
+                                                               dos);
         if (cudaGetLastError() != cudaSuccess) return TETRA_ECUDA;
         return TETRA_OK;
     }

@@ -97,6 +97,34 @@ def test_integrated_64cube_sampled(T):
     assert np.max(np.abs(g[:, idx] - r)) <= TOL * np.max(np.abs(g))
 
 
+def test_integrated_grid_of_several_energy_chunks(T):
+    """6000 energies with 8 orbitals span three shared-memory tiles. Each chunk
+    puts the full step of every tetrahedron below it on its first energy, so
+    every value is the same integer sum as in a plan over any slice of the grid
+    that contains it (the fixed-point unit of this mode does not depend on the
+    grid), and the chunked result matches the oracle at sampled energies."""
+    n = (12, 10, 9)
+    _, eps, w = tb_problem(3, n)
+    omega = energy_window(eps, 6000, pad=0.3)
+    g = run(T, eps, w, n, omega)
+    for a, b in [(0, 1700), (1700, 3900), (3900, 6000), (1999, 2002), (4321, 4322)]:
+        assert np.array_equal(g[:, a:b], run(T, eps, w, n, omega[a:b])), (a, b)
+    idx = np.unique(np.concatenate([np.linspace(0, 5999, 19).astype(int), [1999, 2000, 2001, 3999, 4000]]))
+    r = oracle.dos(eps, w, *n, omega[idx].astype(np.float64), mode="integrated", nthreads=NTHREADS)
+    parity(g[:, idx], r)
+    np.testing.assert_allclose(g[:, -1], w.astype(np.float64).sum(1).mean(0), rtol=1e-5)
+    # occupations do not decrease with E (up to one fixed-point rounding per item)
+    assert np.min(np.diff(g, axis=1)) >= -1e-6 * np.max(g)
+    # a non-uniform grid of several chunks (spacing growing towards the top)
+    x = np.linspace(0.0, 1.0, 5000)
+    lo, hi = float(eps.min()) - 0.2, float(eps.max()) + 0.2
+    om2 = (lo + (hi - lo) * (0.3 * x + 0.7 * x ** 3)).astype(np.float32)
+    g2 = run(T, eps, w, n, om2)
+    idx2 = np.linspace(0, 4999, 17).astype(int)
+    r2 = oracle.dos(eps, w, *n, om2[idx2].astype(np.float64), mode="integrated", nthreads=NTHREADS)
+    parity(g2[:, idx2], r2)
+
+
 @pytest.mark.parametrize("n_electrons", [0.37, 2.0, 5.25])
 def test_fermi_level_matches_oracle(T, n_electrons):
     n = (12, 11, 10)
