@@ -46,8 +46,8 @@ OPS_PER_ITEM = 40
 # hex digits of the SHA-256 of csrc/dos.cu up to the reduce kernels (the
 # forward kernel and every device function it calls); otherwise the bench
 # reports null.
-DOS_TRAFFIC_CAPTURE = {"dos_fwd_sha256": "b897e6a8160c7f30", "grid": 128, "n_omega": 4000,
-                       "bytes": 692142848 + 4363264}
+DOS_TRAFFIC_CAPTURE = {"dos_fwd_sha256": "3ddeea97f2fb5a4a", "grid": 128, "n_omega": 4000,
+                       "bytes": 691929856 + 4707840}
 DOS_FWD_END = b"// Single model: dos[s][w0+j] = u * sum over CTAs of the int64 partials (exact)."
 
 
@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip e2e and extra measurements")
     ap.add_argument("--variant", default=None,
                     choices=["differentiation", "paper_shape", "lindhard", "spectral_t0", "chi0_real_t0",
-                             "near_balance"],
+                             "near_balance", "integrated"],
                     help="run one extra workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -522,7 +522,8 @@ def paper_shape_workload(torch, T, steps, warmup, local):
 
 def integrated_workload(torch, T, n, eps, w, steps, warmup, local):
     """The orbital occupation n_s(E) (TETRA_INTEGRATED mode) at 1000 energies
-    over the band window, and the Fermi level of half filling (4 of 8 bands),
+    over the band window (one energy chunk) and at 6000 (three chunks), and
+    the Fermi level of half filling (4 of 8 bands; one untimed call first),
     on the benchmark's own eigen-data."""
     dev = torch.device("cuda", local)
     nw = 1000
@@ -544,13 +545,29 @@ def integrated_workload(torch, T, n, eps, w, steps, warmup, local):
     torch.cuda.synchronize()
     assert plan.status() == T.TETRA_OK
     ms = a.elapsed_time(b) / steps
+    top = float(out[:, -1].sum())
+    nw6 = 6000
+    plan6 = T.Plan(n, n, n, 8, 8, nw6, mode="integrated", device=local)
+    omega6 = torch.from_numpy(tbgen.uniform_grid(lo, hi, nw6)).to(dev)
+    out6 = torch.empty((8, nw6), dtype=torch.float32, device=dev)
+    plan6.dos(eps, w, omega6, out=out6)
+    torch.cuda.synchronize()
+    a.record(s_)
+    for _ in range(steps):
+        plan6.dos(eps, w, omega6, out=out6)
+    b.record(s_)
+    torch.cuda.synchronize()
+    assert plan6.status() == T.TETRA_OK
+    ms6 = a.elapsed_time(b) / steps
+    plan.fermi_level(eps, w, 4.0)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     ef = plan.fermi_level(eps, w, 4.0)
     fermi_s = time.perf_counter() - t0
-    return {"workload": f"occupation n_s(E) at {nw} energies and the Fermi level of 4 electrons per spin, "
-                        f"{n}^3 grid, 8 bands, 8 orbitals, FP32",
-            "integrated_ms": ms, "fermi_level_eV": ef, "fermi_level_seconds": fermi_s,
-            "total_occupation_top": float(out[:, -1].sum())}
+    return {"workload": f"occupation n_s(E) at {nw} and at {nw6} energies and the Fermi level of 4 electrons "
+                        f"per spin, {n}^3 grid, 8 bands, 8 orbitals, FP32",
+            "integrated_ms": ms, "integrated_6000_ms": ms6, "fermi_level_eV": ef, "fermi_level_seconds": fermi_s,
+            "total_occupation_top": top}
 
 
 def lindhard_workload(torch, T, steps, warmup, local):
@@ -821,6 +838,12 @@ def main():
             p_np, R_np = model_arrays(tbgen.tb_model(rank, n_orb=8))
             r = near_balance_workload(torch, T, args.grid, torch.from_numpy(p_np).to(dev),
                                       torch.from_numpy(R_np).to(dev), args.steps, args.warmup, local)
+        elif args.variant == "integrated":
+            p_np, R_np = model_arrays(tbgen.tb_model(rank, n_orb=8))
+            n = args.grid
+            plan = T.Plan(n, n, n, 8, 8, args.n_omega, device=local)
+            eps, w = plan.eig(torch.from_numpy(p_np).to(dev), torch.from_numpy(R_np).to(dev))
+            r = integrated_workload(torch, T, n, eps, w, args.steps, args.warmup, local)
         else:
             fn = {"differentiation": differentiation_workload, "paper_shape": paper_shape_workload,
                   "lindhard": lindhard_workload, "spectral_t0": spectral_t0_workload,

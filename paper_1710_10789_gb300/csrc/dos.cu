@@ -762,7 +762,15 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                         s_K[it] = (unsigned short)K;
                     }
                     const bool act = it < A.items_per_box && (K > 0 || (MODE == TETRA_INTEGRATED && lo + K < w0 + wc));
-                    if (act) atomicAdd(&khist[min(K, kKBins - 1)], 1);
+                    if constexpr (MODE == TETRA_INTEGRATED && Cfg<MODE, NORB>::pairs) {
+                        // items with an empty window (only a step: every tetrahedron
+                        // below the chunk) all count in bin 0, one add per warp
+                        const unsigned zm = __ballot_sync(0xffffffffu, act && K == 0);
+                        if (act && K > 0) atomicAdd(&khist[min(K, kKBins - 1)], 1);
+                        if (zm && lane == __ffs(zm) - 1) atomicAdd(&khist[0], __popc(zm));
+                    } else {
+                        if (act) atomicAdd(&khist[min(K, kKBins - 1)], 1);
+                    }
                 }
             }
         }
@@ -793,7 +801,20 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             const int K = it < A.items_per_box ? (int)s_K[it] : 0;
             const bool act = it < A.items_per_box &&
                              (K > 0 || (MODE == TETRA_INTEGRATED && s_lo[it] + K < wc));
-            if (act) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
+            if constexpr (MODE == TETRA_INTEGRATED && Cfg<MODE, NORB>::pairs) {
+                // empty windows: consecutive ranks from one cursor add per warp
+                const unsigned zm = __ballot_sync(0xffffffffu, act && K == 0);
+                if (act && K > 0) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
+                if (zm) {
+                    const int lead = __ffs(zm) - 1;
+                    int zb = 0;
+                    if (lane == lead) zb = atomicAdd(&kcursor[0], __popc(zm));
+                    zb = __shfl_sync(0xffffffffu, zb, lead);
+                    if (act && K == 0) s_list[zb + __popc(zm & ((1u << lane) - 1u))] = (unsigned short)it;
+                }
+            } else {
+                if (act) s_list[atomicAdd(&kcursor[min(K, kKBins - 1)], 1)] = (unsigned short)it;
+            }
         }
         // the box's weights (loaded while pass A and the ranking ran), and
         // Bmax = max |w| over them (all of the box, padding included, so it
@@ -850,6 +871,9 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
             const uint32_t gcube = (uint32_t)(gx0 + cx) +
                                    (uint32_t)M.n1 * ((uint32_t)(gy0 + cy) + (uint32_t)M.n2 * (uint32_t)(gz0 + cz));
             if constexpr (Cfg<MODE, NORB>::pairs) {
+                // integrated mode: the lanes that hold an item, for the warp sums of
+                // the steps on the chunk's first energy
+                const unsigned vmask = (MODE == TETRA_INTEGRATED) ? __ballot_sync(0xffffffffu, valid) : 0u;
                 if (!valid) continue;
                 // ---- a pair of tetrahedra sharing a face, walked over the union window
                 const int pr = rest % 3, n = rest / 3;
@@ -890,15 +914,18 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     // above E1 (a flat tetrahedron, E1 = E4, is empty at E = E1)
                     const int hsa = max(hia + 1, loa), hsb = max(hib + 1, lob);
                     const bool stepa = hsa < w0 + wc, stepb = hsb < w0 + wc;
+                    // steps on the chunk's first energy (there go the steps of all
+                    // tetrahedra below the chunk) are summed over the warp first
+                    const bool firsta = fast && stepa && hsa == w0, firstb = fast && stepb && hsb == w0;
+                    const unsigned qbnd = fast ? (unsigned)qmax + 2u : 0u;
                     if (fast) {
-                        const unsigned qbnd = (unsigned)qmax + 2u;
                         if (hi >= lo) {
                             for (int bk = (lo - w0) >> 6; bk <= ((hi - w0) >> 6); ++bk) atomicAdd(&blk_bound[bk], qbnd);
                             atomicAdd(&tile[(lo - w0) * TS + CNT], 1);
                             atomicAdd(&tile[(hi + 1 - w0) * TS + CNT], -1);
                         }
-                        if (stepa) atomicAdd(&blk_bound[(hsa - w0) >> 6], qbnd);
-                        if (stepb) atomicAdd(&blk_bound[(hsb - w0) >> 6], qbnd);
+                        if (stepa && !firsta) atomicAdd(&blk_bound[(hsa - w0) >> 6], qbnd);
+                        if (stepb && !firstb) atomicAdd(&blk_bound[(hsb - w0) >> 6], qbnd);
                     }
                     Tet TA, TB;
                     tet_setup(TA, ea[0], ea[1], ea[2], ea[3], fq);
@@ -908,6 +935,20 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                     for (int s = 0; s < NORB; ++s) {
                         sa[s] = fq * ((ba[0][s] + ba[1][s]) + (ba[2][s] + ba[3][s]));
                         sb[s] = fq * ((bb[0][s] + bb[1][s]) + (bb[2][s] + bb[3][s]));
+                    }
+                    if (__any_sync(vmask, firsta || firstb)) {
+                        // the warp's first-energy steps (a tetrahedron whose step is
+                        // there adds nothing in the window): integer sums, one add per orbital
+                        const bool lead = lane == __ffs(vmask) - 1;
+                        const unsigned bsum = __reduce_add_sync(vmask, (firsta ? qbnd : 0u) + (firstb ? qbnd : 0u));
+                        if (lead && bsum) atomicAdd(&blk_bound[0], bsum);
+#pragma unroll
+                        for (int s = 0; s < NORB; ++s) {
+                            const int v = (firsta ? __float_as_int(sa[s] + dith + kMagic) - kMagicBits : 0) +
+                                          (firstb ? __float_as_int(sb[s] + dith + kMagic) - kMagicBits : 0);
+                            const int tot = __reduce_add_sync(vmask, v);
+                            if (lead && tot) atomicAdd(&stile[s], tot);
+                        }
                     }
                     if (fast) {
                         const int K = hi - lo + 1;
@@ -933,9 +974,9 @@ __global__ void __maxnreg__((Cfg<MODE, NORB>::max_regs))
                         }
 #pragma unroll
                         for (int s = 0; s < NORB; ++s) {
-                            if (stepa)
+                            if (stepa && !firsta)
                                 atomicAdd(&stile[(hsa - w0) * NORB + s], __float_as_int(sa[s] + dith + kMagic) - kMagicBits);
-                            if (stepb)
+                            if (stepb && !firstb)
                                 atomicAdd(&stile[(hsb - w0) * NORB + s], __float_as_int(sb[s] + dith + kMagic) - kMagicBits);
                         }
                     } else {
